@@ -1,0 +1,525 @@
+/*
+ * gv_oracle.c -- CPU oracle for the geometry queries and the navigation step.
+ *
+ * TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the CPU
+ * baseline of the benchmark, never by the CUDA library.  It shares no code with
+ * the library.  Every quantity is IEEE binary64; the file is compiled with
+ * -ffp-contract=off so that no multiply-add is fused.
+ *
+ * What it computes (the three questions of the VecGeom section, and the
+ * navigation step of the Physics / Detector geometry subsections):
+ *
+ *   Each solid is a set of constraints g_i(p) (in mm, negative = satisfied).
+ *   s(p) = max_i g_i(p) is the decision quantity.  The point is INSIDE if
+ *   s < -h, OUTSIDE if s > h, SURFACE otherwise, with h = 0.5e-9 mm.
+ *
+ *   Safety:   SafetyToIn  = s  (OUTSIDE), 0 (SURFACE), -1 (INSIDE, wrong side)
+ *             SafetyToOut = -s (INSIDE),  0 (SURFACE), -1 (OUTSIDE)
+ *             (polycone: per-section closed constraint sets, see below).
+ *
+ *   Distance: every root t > 0 of every constraint surface along p + t d is a
+ *   candidate; the gaps between consecutive candidates are classified inside or
+ *   outside by the sign of s at their midpoint (no tolerance).
+ *   DistanceToIn:  INSIDE -> -1; SURFACE and entering -> 0; otherwise the first
+ *                  candidate after which the gap is inside; none -> +inf.
+ *   DistanceToOut: OUTSIDE -> -1; SURFACE and leaving -> 0; otherwise the first
+ *                  candidate after which the gap is outside.
+ *   A SURFACE point is "leaving" when some constraint within the band
+ *   (g_i >= -h) grows along d, and "entering" when every such constraint
+ *   decreases along d.
+ */
+#include "gv_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define H OR_HALF_TOL
+#define MAXROOTS 512
+
+int or_solid_size(void) { return (int)sizeof(or_solid); }
+
+/* ------------------------------------------------------------------ setup */
+
+static void set_plane(or_plane* P, double nx, double ny, double nz, double c) {
+  P->n[0] = nx; P->n[1] = ny; P->n[2] = nz; P->c = c;
+}
+
+static double dot3(const double a[3], const double b[3]) {
+  return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+int or_setup_box(double dx, double dy, double dz, or_solid* s) {
+  if (!(dx > 0 && dy > 0 && dz > 0) || !isfinite(dx + dy + dz)) return -1;
+  memset(s, 0, sizeof(*s));
+  s->type = OR_BOX; s->family = 0; s->nplanes = 6;
+  set_plane(&s->pl[0], 0, 0, -1, dz);
+  set_plane(&s->pl[1], 0, 0, 1, dz);
+  set_plane(&s->pl[2], 0, -1, 0, dy);
+  set_plane(&s->pl[3], 0, 1, 0, dy);
+  set_plane(&s->pl[4], -1, 0, 0, dx);
+  set_plane(&s->pl[5], 1, 0, 0, dx);
+  return 0;
+}
+
+/* A side face through the quad (A, B, C, D): normal from the cross product of
+ * the diagonals, oriented away from the solid's vertex centroid, normalised;
+ * the offset is the mean of n.V over the four vertices. */
+static int face_plane(const double A[3], const double B[3], const double C[3],
+                      const double D[3], const double cs[3], or_plane* P) {
+  double u[3], w[3], n[3], cf[3], e[3];
+  for (int i = 0; i < 3; i++) { u[i] = C[i] - A[i]; w[i] = D[i] - B[i]; }
+  n[0] = u[1] * w[2] - u[2] * w[1];
+  n[1] = u[2] * w[0] - u[0] * w[2];
+  n[2] = u[0] * w[1] - u[1] * w[0];
+  for (int i = 0; i < 3; i++) { cf[i] = ((A[i] + B[i]) + (C[i] + D[i])) * 0.25; e[i] = cf[i] - cs[i]; }
+  if (dot3(n, e) < 0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+  double len = sqrt(dot3(n, n));
+  if (!(len > 0)) return -1;
+  for (int i = 0; i < 3; i++) n[i] = n[i] / len;
+  double c = ((dot3(n, A) + dot3(n, B)) + (dot3(n, C) + dot3(n, D))) * 0.25;
+  const double* V[4] = {A, B, C, D};
+  for (int i = 0; i < 4; i++)
+    if (fabs(dot3(n, V[i]) - c) > 1e-9) return -1; /* not planar */
+  set_plane(P, n[0], n[1], n[2], c);
+  return 0;
+}
+
+/* General trapezoid, parameters (dz, theta, phi, dy1, dx1, dx2, alpha1,
+ * dy2, dx3, dx4, alpha2): the faces at z = -dz and z = +dz are trapezoids
+ * whose centres lie on the line of polar angle theta and azimuth phi through
+ * the origin; on the face at -dz the half-length in y is dy1, the half-lengths
+ * in x at y = -dy1 and y = +dy1 are dx1 and dx2, and the face is sheared by
+ * alpha1 (x offset y tan alpha1); likewise dy2, dx3, dx4, alpha2 at +dz. */
+int or_setup_trap(const double p[11], or_solid* s) {
+  const double dz = p[0], th = p[1], ph = p[2];
+  for (int i = 0; i < 11; i++) if (!isfinite(p[i])) return -1;
+  if (!(dz > 0 && p[3] > 0 && p[4] > 0 && p[5] > 0 && p[7] > 0 && p[8] > 0 && p[9] > 0)) return -1;
+  if (!(fabs(th) < 1.5707963267948966 && fabs(p[6]) < 1.5707963267948966 &&
+        fabs(p[10]) < 1.5707963267948966)) return -1;
+  memset(s, 0, sizeof(*s));
+  s->type = OR_TRAP; s->family = 0; s->nplanes = 6;
+  const double tthc = tan(th) * cos(ph), tths = tan(th) * sin(ph);
+  double v[8][3];
+  for (int j = 0; j < 2; j++) {
+    const double zf = j == 0 ? -dz : dz;
+    const double dy = j == 0 ? p[3] : p[7];
+    const double dxa = j == 0 ? p[4] : p[8];
+    const double dxb = j == 0 ? p[5] : p[9];
+    const double ta = tan(j == 0 ? p[6] : p[10]);
+    const double cx = zf * tthc, cy = zf * tths;
+    const double xm = cx - dy * ta, xp = cx + dy * ta;
+    v[4 * j + 0][0] = xm - dxa; v[4 * j + 0][1] = cy - dy; v[4 * j + 0][2] = zf;
+    v[4 * j + 1][0] = xm + dxa; v[4 * j + 1][1] = cy - dy; v[4 * j + 1][2] = zf;
+    v[4 * j + 2][0] = xp - dxb; v[4 * j + 2][1] = cy + dy; v[4 * j + 2][2] = zf;
+    v[4 * j + 3][0] = xp + dxb; v[4 * j + 3][1] = cy + dy; v[4 * j + 3][2] = zf;
+  }
+  double cs[3];
+  for (int i = 0; i < 3; i++) {
+    double acc = 0;
+    for (int k = 0; k < 8; k++) acc = acc + v[k][i];
+    cs[i] = acc * 0.125;
+  }
+  set_plane(&s->pl[0], 0, 0, -1, dz);
+  set_plane(&s->pl[1], 0, 0, 1, dz);
+  if (face_plane(v[0], v[1], v[5], v[4], cs, &s->pl[2])) return -1; /* -y */
+  if (face_plane(v[2], v[6], v[7], v[3], cs, &s->pl[3])) return -1; /* +y */
+  if (face_plane(v[0], v[4], v[6], v[2], cs, &s->pl[4])) return -1; /* -x */
+  if (face_plane(v[1], v[3], v[7], v[5], cs, &s->pl[5])) return -1; /* +x */
+  return 0;
+}
+
+int or_setup_trd(double dx1, double dx2, double dy1, double dy2, double dz, or_solid* s) {
+  const double p[11] = {dz, 0, 0, dy1, dx1, dx1, 0, dy2, dx2, dx2, 0};
+  int rc = or_setup_trap(p, s);
+  if (rc == 0) s->type = OR_TRD;
+  return rc;
+}
+
+static void set_line(or_line* L, double r0, double r1, double z0, double z1) {
+  L->a = (r1 - r0) / (z1 - z0);
+  L->b = r0 - L->a * z0;
+  L->k = 1.0 / sqrt(1.0 + L->a * L->a);
+}
+
+int or_setup_pcon(int nz, const double* z, const double* rmin, const double* rmax,
+                  double sphi, double dphi, or_solid* s) {
+  if (nz < 2 || nz > OR_MAXZ) return -1;
+  if (!isfinite(sphi) || !isfinite(dphi) || !(dphi > 0)) return -1;
+  for (int k = 0; k < nz; k++) {
+    if (!isfinite(z[k]) || !isfinite(rmin[k]) || !isfinite(rmax[k])) return -1;
+    if (!(rmin[k] >= 0 && rmin[k] < rmax[k])) return -1;
+    if (k > 0 && !(z[k] > z[k - 1])) return -1;
+  }
+  memset(s, 0, sizeof(*s));
+  s->type = OR_PCON; s->family = 1; s->nz = nz;
+  for (int k = 0; k < nz; k++) s->z[k] = z[k];
+  for (int k = 0; k + 1 < nz; k++) {
+    set_line(&s->out[k], rmax[k], rmax[k + 1], z[k], z[k + 1]);
+    s->out[k].present = 1;
+    set_line(&s->in[k], rmin[k], rmin[k + 1], z[k], z[k + 1]);
+    s->in[k].present = (rmin[k] > 0 || rmin[k + 1] > 0);
+  }
+  const double twopi = 6.283185307179586, pi = 3.141592653589793;
+  s->has_phi = dphi < twopi;
+  s->phi_wide = dphi > pi;
+  const double ephi = sphi + dphi;
+  s->ns[0] = sin(sphi);  s->ns[1] = -cos(sphi);
+  s->ne[0] = -sin(ephi); s->ne[1] = cos(ephi);
+  return 0;
+}
+
+int or_setup_tube(double rmin, double rmax, double dz, double sphi, double dphi, or_solid* s) {
+  if (!(dz > 0)) return -1;
+  const double z[2] = {-dz, dz}, rn[2] = {rmin, rmin}, rx[2] = {rmax, rmax};
+  int rc = or_setup_pcon(2, z, rn, rx, sphi, dphi, s);
+  if (rc == 0) s->type = OR_TUBE;
+  return rc;
+}
+
+int or_setup_cone(double rmin1, double rmax1, double rmin2, double rmax2, double dz,
+                  double sphi, double dphi, or_solid* s) {
+  if (!(dz > 0)) return -1;
+  const double z[2] = {-dz, dz}, rn[2] = {rmin1, rmin2}, rx[2] = {rmax1, rmax2};
+  int rc = or_setup_pcon(2, z, rn, rx, sphi, dphi, s);
+  if (rc == 0) s->type = OR_CONE;
+  return rc;
+}
+
+/* ------------------------------------------------------ constraint values */
+
+static double plane_g(const or_plane* P, const double p[3]) {
+  return ((P->n[0] * p[0] + P->n[1] * p[1]) + P->n[2] * p[2]) - P->c;
+}
+static double line_out_g(const or_line* L, double r, double z) { return (r - (L->a * z + L->b)) * L->k; }
+static double line_in_g(const or_line* L, double r, double z) { return ((L->a * z + L->b) - r) * L->k; }
+static double rho(const double p[3]) { return sqrt(p[0] * p[0] + p[1] * p[1]); }
+static double phi_plane(const double n[2], const double p[3]) { return n[0] * p[0] + n[1] * p[1]; }
+
+static double phi_g(const or_solid* s, const double p[3]) {
+  const double a = phi_plane(s->ns, p), b = phi_plane(s->ne, p);
+  return s->phi_wide ? (a < b ? a : b) : (a > b ? a : b);
+}
+
+static int section_of(const or_solid* s, double z) {
+  int k = 0;
+  while (k < s->nz - 2 && z >= s->z[k + 1]) k++;
+  return k;
+}
+
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+
+double or_s_code(const or_solid* s, const double p[3]) {
+  if (s->family == 0) {
+    double v = plane_g(&s->pl[0], p);
+    for (int i = 1; i < s->nplanes; i++) v = dmax(v, plane_g(&s->pl[i], p));
+    return v;
+  }
+  const double r = rho(p), z = p[2];
+  const int k = section_of(s, z);
+  double v = line_out_g(&s->out[k], r, z);
+  v = dmax(v, s->z[0] - z);
+  v = dmax(v, z - s->z[s->nz - 1]);
+  if (s->in[k].present) v = dmax(v, line_in_g(&s->in[k], r, z));
+  if (s->has_phi) v = dmax(v, phi_g(s, p));
+  return v;
+}
+
+/* Polycone section k as a closed piece, its own z-planes included. */
+static double s_closed(const or_solid* s, int k, const double p[3]) {
+  const double r = rho(p), z = p[2];
+  double v = line_out_g(&s->out[k], r, z);
+  v = dmax(v, s->z[k] - z);
+  v = dmax(v, z - s->z[k + 1]);
+  if (s->in[k].present) v = dmax(v, line_in_g(&s->in[k], r, z));
+  if (s->has_phi) v = dmax(v, phi_g(s, p));
+  return v;
+}
+
+static int code_of(double v) { return v < -H ? OR_INSIDE : (v > H ? OR_OUTSIDE : OR_SURFACE); }
+
+int or_inside(const or_solid* s, const double p[3]) { return code_of(or_s_code(s, p)); }
+
+double or_safety_in(const or_solid* s, const double p[3]) {
+  const double v = or_s_code(s, p);
+  const int c = code_of(v);
+  if (c == OR_INSIDE) return -1.0;
+  if (c == OR_SURFACE) return 0.0;
+  if (s->family == 0) return v;
+  double best = s_closed(s, 0, p);
+  for (int k = 1; k + 1 < s->nz; k++) best = dmin(best, s_closed(s, k, p));
+  return best;
+}
+
+double or_safety_out(const or_solid* s, const double p[3]) {
+  const double v = or_s_code(s, p);
+  const int c = code_of(v);
+  if (c == OR_OUTSIDE) return -1.0;
+  if (c == OR_SURFACE) return 0.0;
+  if (s->family == 0) return -v;
+  return -s_closed(s, section_of(s, p[2]), p);
+}
+
+/* ------------------------------------------- surface start: in or out? */
+
+/* Over the constraints of s at p that lie within the band (g >= -h): does any
+ * grow along d (leaving), and does every one shrink along d (entering)? */
+static void surface_motion(const or_solid* s, const double p[3], const double d[3],
+                           int* leaving, int* entering) {
+  double g[8], gd[8];
+  int m = 0;
+  if (s->family == 0) {
+    for (int i = 0; i < s->nplanes; i++) { g[m] = plane_g(&s->pl[i], p); gd[m] = dot3(s->pl[i].n, d); m++; }
+  } else {
+    const double r = rho(p), z = p[2];
+    const int k = section_of(s, z);
+    const double radial = p[0] * d[0] + p[1] * d[1];
+    g[m] = line_out_g(&s->out[k], r, z); gd[m] = radial - s->out[k].a * d[2] * r; m++;
+    if (s->in[k].present) { g[m] = line_in_g(&s->in[k], r, z); gd[m] = -(radial - s->in[k].a * d[2] * r); m++; }
+    g[m] = s->z[0] - z; gd[m] = -d[2]; m++;
+    g[m] = z - s->z[s->nz - 1]; gd[m] = d[2]; m++;
+    if (s->has_phi) {
+      const double a = phi_plane(s->ns, p), b = phi_plane(s->ne, p);
+      const double ad = phi_plane(s->ns, d), bd = phi_plane(s->ne, d);
+      if (s->phi_wide) {
+        if (a <= b) { g[m] = a; gd[m] = ad; } else { g[m] = b; gd[m] = bd; }
+        m++;
+      } else {
+        g[m] = a; gd[m] = ad; m++;
+        g[m] = b; gd[m] = bd; m++;
+      }
+    }
+  }
+  int any_out = 0, all_in = 1;
+  for (int i = 0; i < m; i++) {
+    if (g[i] >= -H) {
+      if (gd[i] > 0) any_out = 1;
+      if (!(gd[i] < 0)) all_in = 0;
+    }
+  }
+  *leaving = any_out;
+  *entering = all_in;
+}
+
+/* ------------------------------------------------- candidate crossings */
+
+static void add_root(double* t, int* m, double v) {
+  if (v > 0 && isfinite(v) && *m < MAXROOTS) t[(*m)++] = v;
+}
+
+/* Crossings of the surface r = a z + b (a z + b >= 0) by p + t d: the roots of
+ * A t^2 + 2 B t + C = 0, by the cancellation-free pair q/A, C/q. */
+static void cone_roots(const or_line* L, const double p[3], const double d[3], double* t, int* m) {
+  const double P = L->a * p[2] + L->b, D = L->a * d[2];
+  const double A = (d[0] * d[0] + d[1] * d[1]) - D * D;
+  const double B = (p[0] * d[0] + p[1] * d[1]) - P * D;
+  const double C = (p[0] * p[0] + p[1] * p[1]) - P * P;
+  double r[2]; int nr = 0;
+  if (A == 0) {
+    if (B != 0) r[nr++] = -C / (2 * B);
+  } else {
+    const double disc = B * B - A * C;
+    if (disc > 0) {
+      const double sq = sqrt(disc);
+      const double q = -(B + (B >= 0 ? sq : -sq));
+      r[nr++] = q / A;
+      if (q != 0) r[nr++] = C / q;
+    }
+  }
+  for (int i = 0; i < nr; i++) {
+    const double zr = p[2] + r[i] * d[2];
+    if (L->a * zr + L->b >= 0) add_root(t, m, r[i]);
+  }
+}
+
+static void plane_root(const double n[3], double c, const double p[3], const double d[3],
+                       double* t, int* m) {
+  const double nd = dot3(n, d);
+  if (nd != 0) add_root(t, m, (c - dot3(n, p)) / nd);
+}
+
+static int cmp_double(const void* a, const void* b) {
+  const double x = *(const double*)a, y = *(const double*)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static int candidates(const or_solid* s, const double p[3], const double d[3], double* t) {
+  int m = 0;
+  if (s->family == 0) {
+    for (int i = 0; i < s->nplanes; i++) plane_root(s->pl[i].n, s->pl[i].c, p, d, t, &m);
+  } else {
+    for (int k = 0; k + 1 < s->nz; k++) {
+      cone_roots(&s->out[k], p, d, t, &m);
+      if (s->in[k].present) cone_roots(&s->in[k], p, d, t, &m);
+    }
+    const double ez[3] = {0, 0, 1};
+    for (int k = 0; k < s->nz; k++) plane_root(ez, s->z[k], p, d, t, &m);
+    if (s->has_phi) {
+      const double n1[3] = {s->ns[0], s->ns[1], 0}, n2[3] = {s->ne[0], s->ne[1], 0};
+      plane_root(n1, 0, p, d, t, &m);
+      plane_root(n2, 0, p, d, t, &m);
+    }
+  }
+  qsort(t, (size_t)m, sizeof(double), cmp_double);
+  int u = 0;
+  for (int i = 0; i < m; i++)
+    if (u == 0 || t[i] != t[u - 1]) t[u++] = t[i];
+  return u;
+}
+
+/* Inside (no tolerance) on the gap that follows candidate j-1 (gap 0 starts at t = 0). */
+static int gap_inside(const or_solid* s, const double p[3], const double d[3],
+                      const double* t, int m, int j) {
+  const double lo = j == 0 ? 0.0 : t[j - 1];
+  const double mid = j < m ? 0.5 * (lo + t[j]) : 2.0 * lo + 1.0;
+  const double q[3] = {p[0] + mid * d[0], p[1] + mid * d[1], p[2] + mid * d[2]};
+  return or_s_code(s, q) <= 0;
+}
+
+double or_dist_in(const or_solid* s, const double p[3], const double d[3]) {
+  const int c = or_inside(s, p);
+  if (c == OR_INSIDE) return -1.0;
+  if (c == OR_SURFACE) {
+    int leaving, entering;
+    surface_motion(s, p, d, &leaving, &entering);
+    if (entering) return 0.0;
+  }
+  double t[MAXROOTS];
+  const int m = candidates(s, p, d, t);
+  for (int j = 1; j <= m; j++)
+    if (gap_inside(s, p, d, t, m, j)) return t[j - 1];
+  return INFINITY;
+}
+
+double or_dist_out(const or_solid* s, const double p[3], const double d[3]) {
+  const int c = or_inside(s, p);
+  if (c == OR_OUTSIDE) return -1.0;
+  if (c == OR_SURFACE) {
+    int leaving, entering;
+    surface_motion(s, p, d, &leaving, &entering);
+    if (leaving) return 0.0;
+  }
+  double t[MAXROOTS];
+  const int m = candidates(s, p, d, t);
+  for (int j = 1; j <= m; j++)
+    if (!gap_inside(s, p, d, t, m, j)) return t[j - 1];
+  return INFINITY; /* a bounded solid is always left: reaching here is a bug */
+}
+
+void or_query(const or_solid* s, int64_t n,
+              const double* x, const double* y, const double* z,
+              const double* dx, const double* dy, const double* dz,
+              int8_t* inside, double* dist_in, double* dist_out,
+              double* safety_in, double* safety_out, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+  for (int64_t i = 0; i < n; i++) {
+    const double p[3] = {x[i], y[i], z[i]};
+    if (inside) inside[i] = (int8_t)or_inside(s, p);
+    if (safety_in) safety_in[i] = or_safety_in(s, p);
+    if (safety_out) safety_out[i] = or_safety_out(s, p);
+    if (dist_in || dist_out) {
+      const double d[3] = {dx[i], dy[i], dz[i]};
+      if (dist_in) dist_in[i] = or_dist_in(s, p, d);
+      if (dist_out) dist_out[i] = or_dist_out(s, p, d);
+    }
+  }
+}
+
+void or_s_code_n(const or_solid* s, int64_t n, const double* x, const double* y,
+                 const double* z, double* out) {
+  for (int64_t i = 0; i < n; i++) {
+    const double p[3] = {x[i], y[i], z[i]};
+    out[i] = or_s_code(s, p);
+  }
+}
+
+/* -------------------------------------------------------------- navigation */
+
+void or_compose(int nnodes, const int32_t* parent, const double* RL, const double* tl,
+                double* RG, double* tg) {
+  for (int v = 0; v < nnodes; v++) {
+    const double* L = RL + 9 * v;
+    double* G = RG + 9 * v;
+    if (parent[v] < 0) {
+      for (int i = 0; i < 9; i++) G[i] = L[i];
+      for (int i = 0; i < 3; i++) tg[3 * v + i] = tl[3 * v + i];
+      continue;
+    }
+    const double* P = RG + 9 * parent[v];
+    const double* tp = tg + 3 * parent[v];
+    for (int i = 0; i < 3; i++) {
+      for (int j = 0; j < 3; j++)
+        G[3 * i + j] = (P[3 * i + 0] * L[0 * 3 + j] + P[3 * i + 1] * L[1 * 3 + j]) + P[3 * i + 2] * L[2 * 3 + j];
+      tg[3 * v + i] = ((P[3 * i + 0] * tl[3 * v + 0] + P[3 * i + 1] * tl[3 * v + 1]) +
+                       P[3 * i + 2] * tl[3 * v + 2]) + tp[i];
+    }
+  }
+}
+
+/* World to the frame of a node: p_local = R^T (p - t), d_local = R^T d. */
+static void to_local(const double* R, const double* t, const double p[3], const double d[3],
+                     double pl[3], double dl[3]) {
+  const double v[3] = {p[0] - t[0], p[1] - t[1], p[2] - t[2]};
+  for (int i = 0; i < 3; i++) {
+    pl[i] = (R[0 * 3 + i] * v[0] + R[1 * 3 + i] * v[1]) + R[2 * 3 + i] * v[2];
+    if (d) dl[i] = (R[0 * 3 + i] * d[0] + R[1 * 3 + i] * d[1]) + R[2 * 3 + i] * d[2];
+  }
+}
+
+void or_locate(const or_solid* solids, int nnodes, const int32_t* node_solid,
+               const int32_t* parent, const double* RG, const double* tg,
+               int64_t n, const double* x, const double* y, const double* z,
+               int32_t* node, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+  for (int64_t i = 0; i < n; i++) {
+    const double p[3] = {x[i], y[i], z[i]};
+    double pl[3];
+    to_local(RG, tg, p, NULL, pl, NULL);
+    if (or_inside(&solids[node_solid[0]], pl) == OR_OUTSIDE) { node[i] = -1; continue; }
+    int v = 0, moved = 1;
+    while (moved) {
+      moved = 0;
+      for (int c = 0; c < nnodes; c++) {
+        if (parent[c] != v) continue;
+        to_local(RG + 9 * c, tg + 3 * c, p, NULL, pl, NULL);
+        if (or_inside(&solids[node_solid[c]], pl) != OR_OUTSIDE) { v = c; moved = 1; break; }
+      }
+    }
+    node[i] = v;
+  }
+}
+
+void or_nav_step(const or_solid* solids, int nnodes, const int32_t* node_solid,
+                 const int32_t* parent, const double* RG, const double* tg,
+                 int64_t n, const double* x, const double* y, const double* z,
+                 const double* dx, const double* dy, const double* dz, const int32_t* node,
+                 double* step, double* safety, int32_t* next, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+  for (int64_t i = 0; i < n; i++) {
+    const double p[3] = {x[i], y[i], z[i]}, d[3] = {dx[i], dy[i], dz[i]};
+    const int v = node[i];
+    if (v < 0 || v >= nnodes) { step[i] = -1.0; safety[i] = -1.0; next[i] = -1; continue; }
+    double pl[3], dl[3];
+    to_local(RG + 9 * v, tg + 3 * v, p, d, pl, dl);
+    const or_solid* m = &solids[node_solid[v]];
+    double best = or_dist_out(m, pl, dl);
+    int who = -1, have = best >= 0;
+    double saf = or_safety_out(m, pl);
+    int have_s = saf >= 0;
+    for (int c = 0; c < nnodes; c++) {
+      if (parent[c] != v) continue;
+      to_local(RG + 9 * c, tg + 3 * c, p, d, pl, dl);
+      const or_solid* ds = &solids[node_solid[c]];
+      const double t = or_dist_in(ds, pl, dl);
+      if (t >= 0 && (!have || t < best || (t == best && who == -1))) { best = t; who = c; have = 1; }
+      const double sd = or_safety_in(ds, pl);
+      if (sd >= 0 && (!have_s || sd < saf)) { saf = sd; have_s = 1; }
+    }
+    step[i] = have ? best : -1.0;
+    safety[i] = have_s ? saf : -1.0;
+    next[i] = have ? who : -1;
+  }
+}

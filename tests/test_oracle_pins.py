@@ -1,0 +1,466 @@
+"""Pins of the CPU oracle against what the mathematics fixes.
+
+The paper (VecGeom section) asks three questions of every solid: is the point
+inside, how far is the border (safety), how far can it move along its direction
+(DistanceToIn / DistanceToOut).  The oracle answers them by enumerating surface
+crossings; these tests check it against independent routes: textbook closed
+forms (slab method, cylinder quadratic, radial rays), construction (points placed
+inside / outside / on a face by design), brute-force ray marching with bisection,
+invariants (a returned finite distance lands on the surface; safety never
+exceeds any distance), and reductions (a trd with parallel faces is a box; a
+polycone with a straight profile does not see its internal planes).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+IN, SURF, OUT = oracle.INSIDE, oracle.SURFACE, oracle.OUTSIDE
+H = oracle.HALF_TOL
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+ALL_SPECS = [W.BOX_M1, W.TRD_M3, W.TUBE_M2, W.CONE_M2, W.polycone_m3()] + W.solid_table(18, seed=7)
+
+
+def sol(spec):
+    return oracle.Solid.from_spec(spec)
+
+
+# ------------------------------------------------------------------ box
+
+def test_box_membership_by_construction():
+    D = np.array([10.0, 20.0, 30.0])
+    b = oracle.Solid("box", *D)
+    g = np.random.default_rng(1)
+    inner = g.uniform(-1, 1, (5000, 3)) * (D - 1e-6)
+    assert (b.inside(inner) == IN).all()
+    outer = g.uniform(-1, 1, (5000, 3)) * D
+    ax = g.integers(0, 3, 5000)
+    outer[np.arange(5000), ax] = np.sign(g.uniform(-1, 1, 5000)) * (D[ax] + g.uniform(1e-6, 50, 5000))
+    assert (b.inside(outer) == OUT).all()
+    face = g.uniform(-1, 1, (5000, 3)) * (D - 1e-6)
+    sgn = np.where(g.random(5000) < 0.5, -1.0, 1.0)
+    face[np.arange(5000), ax] = sgn * D[ax]
+    assert (b.inside(face) == SURF).all()
+    # the band is h = 0.5e-9 mm on either side
+    near_in = face.copy(); near_in[np.arange(5000), ax] -= sgn * 0.4e-9
+    near_out = face.copy(); near_out[np.arange(5000), ax] += sgn * 0.4e-9
+    assert (b.inside(near_in) == SURF).all() and (b.inside(near_out) == SURF).all()
+    deep_in = face.copy(); deep_in[np.arange(5000), ax] -= sgn * 0.7e-9
+    far_out = face.copy(); far_out[np.arange(5000), ax] += sgn * 0.7e-9
+    assert (b.inside(deep_in) == IN).all() and (b.inside(far_out) == OUT).all()
+
+
+def _slab(D, p, d):
+    """Textbook slab method for an axis-aligned box (Kay-Kajiya), per track."""
+    tn, tf = -np.inf, np.inf
+    for i in range(3):
+        if d[i] == 0.0:
+            if abs(p[i]) > D[i]:
+                return np.inf, -np.inf
+            continue
+        a, b = (-D[i] - p[i]) / d[i], (D[i] - p[i]) / d[i]
+        tn, tf = max(tn, min(a, b)), min(tf, max(a, b))
+    return tn, tf
+
+
+def test_box_slab_closed_form():
+    D = np.array([10.0, 20.0, 30.0])
+    b = oracle.Solid("box", *D)
+    g = np.random.default_rng(2)
+    n = 20000
+    p = g.uniform(-1, 1, (n, 3)) * 2 * D
+    d = W.isotropic(n, g)
+    # a fifth of the directions axis-parallel or in a coordinate plane (d_i = 0)
+    k = n // 5
+    d[:k, g.integers(0, 3)] = 0.0
+    d[:k] /= np.linalg.norm(d[:k], axis=1, keepdims=True)
+    r = b.query(p[:, 0], p[:, 1], p[:, 2], d[:, 0], d[:, 1], d[:, 2])
+    for i in range(n):
+        tn, tf = _slab(D, p[i], d[i])
+        code = r["inside"][i]
+        if code == IN:
+            assert r["dist_out"][i] == pytest.approx(tf, abs=1e-12)
+            assert r["dist_in"][i] == -1
+            assert r["safety_out"][i] == pytest.approx(np.min(D - np.abs(p[i])), abs=1e-12)
+        elif code == OUT:
+            want = tn if (tn < tf and tn > 0) else np.inf
+            assert r["dist_in"][i] == pytest.approx(want, abs=1e-12) or (np.isinf(want) and np.isinf(r["dist_in"][i]))
+            assert r["dist_out"][i] == -1
+            excess = np.maximum(np.abs(p[i]) - D, 0)
+            # max of the per-axis excesses: exact for one violated axis, a lower bound otherwise
+            assert r["safety_in"][i] == pytest.approx(excess.max(), abs=1e-12)
+            assert r["safety_in"][i] <= np.linalg.norm(excess) + 1e-12
+
+
+# ------------------------------------------------------------- cylinders
+
+def test_full_cylinder_closed_form():
+    R, Z = 20.0, 30.0
+    c = oracle.Solid("tube", 0.0, R, Z, 0.0, 2 * math.pi)
+    g = np.random.default_rng(3)
+    n = 20000
+    p = g.uniform(-1, 1, (n, 3)) * [2 * R, 2 * R, 2 * Z]
+    d = W.isotropic(n, g)
+    r = c.query(p[:, 0], p[:, 1], p[:, 2], d[:, 0], d[:, 1], d[:, 2])
+    for i in range(n):
+        x, y, z = p[i]
+        u, v, w = d[i]
+        A, B, C = u * u + v * v, x * u + y * v, x * x + y * y - R * R
+        rr = math.hypot(x, y)
+        code = r["inside"][i]
+        if code == IN:
+            tr = (-B + math.sqrt(B * B - A * C)) / A if A > 0 else np.inf
+            tz = (math.copysign(Z, w) - z) / w if w != 0 else np.inf
+            assert r["dist_out"][i] == pytest.approx(min(tr, tz), rel=1e-12, abs=1e-12)
+            assert r["safety_out"][i] == pytest.approx(min(R - rr, Z - abs(z)), abs=1e-12)
+        elif code == OUT:
+            best = np.inf
+            disc = B * B - A * C
+            if A > 0 and disc > 0 and C > 0:
+                t = (-B - math.sqrt(disc)) / A
+                if t > 0 and abs(z + t * w) <= Z:
+                    best = t
+            if w != 0 and abs(z) > Z:
+                t = ((-Z if w > 0 else Z) - z) / w
+                q = (x + t * u, y + t * v)
+                if t > 0 and math.hypot(*q) <= R:
+                    best = min(best, t)
+            got = r["dist_in"][i]
+            if np.isinf(best):
+                assert np.isinf(got)
+            else:
+                assert got == pytest.approx(best, rel=1e-10, abs=1e-10)
+            assert r["safety_in"][i] == pytest.approx(max(rr - R, abs(z) - Z), abs=1e-12)
+
+
+def test_tube_radial_rays_closed_form():
+    """Rays from the axis, in the xy-plane, at azimuth a: for a segment (rmin, rmax, 0..270
+    deg) DistanceToIn is rmin inside the phi range and +inf outside it."""
+    t = oracle.Solid("tube", 5.0, 20.0, 30.0, 0.0, 1.5 * math.pi)
+    a = np.linspace(0.01, 2 * math.pi - 0.01, 721)
+    d = np.stack([np.cos(a), np.sin(a), np.zeros_like(a)], 1)
+    z0 = np.zeros_like(a)
+    r = t.query(z0, z0, z0 + 3.0, d[:, 0], d[:, 1], d[:, 2])
+    inrange = a < 1.5 * math.pi
+    assert np.allclose(r["dist_in"][inrange], 5.0, atol=1e-12)
+    assert np.isinf(r["dist_in"][~inrange]).all()
+    # from the middle of the wall outwards, DistanceToOut is rmax - 12.5
+    p = 12.5 * d
+    r = t.query(p[:, 0], p[:, 1], z0, d[:, 0], d[:, 1], d[:, 2])
+    assert np.allclose(r["dist_out"][inrange], 7.5, atol=1e-12)
+    assert (r["inside"][~inrange] == OUT).all()
+
+
+def test_cone_axis_parallel_closed_form():
+    """Rays parallel to the axis inside a cone frustum: exit through the top plane or,
+    where the wall closes in, through the slanted wall at R(z) = r."""
+    rmax1, rmax2, dz = 25.0, 10.0, 40.0
+    c = oracle.Solid("cone", 0.0, rmax1, 0.0, rmax2, dz, 0.0, 2 * math.pi)
+    g = np.random.default_rng(4)
+    n = 5000
+    z = g.uniform(-dz + 1, dz - 1, n)
+    Rz = rmax1 + (z + dz) / (2 * dz) * (rmax2 - rmax1)
+    rr = g.uniform(0, 1, n) * (Rz - 1e-6)
+    ph = g.uniform(0, 2 * math.pi, n)
+    x, y = rr * np.cos(ph), rr * np.sin(ph)
+    one, zero = np.ones(n), np.zeros(n)
+    r = c.query(x, y, z, zero, zero, one)
+    # wall reached where rmax1 + (z' + dz)/(2dz) (rmax2 - rmax1) = rr
+    zw = (rr - rmax1) * (2 * dz) / (rmax2 - rmax1) - dz
+    want = np.where(zw < dz, zw - z, dz - z)
+    assert np.allclose(r["dist_out"], want, rtol=1e-10, atol=1e-10)
+    r = c.query(x, y, z, zero, zero, -one)
+    assert np.allclose(r["dist_out"], z + dz, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------ reductions
+
+def _away_from_band(s):
+    return (np.abs(np.abs(s) - H) > 1e-11)
+
+
+def test_trd_with_parallel_faces_is_a_box():
+    box = oracle.Solid("box", 10, 20, 30)
+    trd = oracle.Solid("trd", 10, 10, 20, 20, 30)
+    t = W.tracks_for_solid(W.BOX_M1, 20000, seed=5)
+    a = box.query(**t)
+    b = trd.query(**t)
+    s = np.array([box.s_code([t["x"][i], t["y"][i], t["z"][i]]) for i in range(20000)])
+    ok = _away_from_band(s)
+    assert ok.mean() > 0.99
+    assert (a["inside"][ok] == b["inside"][ok]).all()
+    for k in ("dist_in", "dist_out", "safety_in", "safety_out"):
+        fin = np.isfinite(a[k]) & ok
+        assert np.allclose(a[k][fin], b[k][fin], rtol=0, atol=1e-12), k
+        assert (np.isinf(a[k][ok]) == np.isinf(b[k][ok])).all()
+
+
+def test_polycone_internal_planes_are_not_surfaces():
+    """A polycone whose extra planes lie on straight segments of the profile is the
+    same solid as without them: same codes, same distances; internal planes are
+    never reported as surfaces."""
+    z2, rn2, rx2 = [-40.0, 40.0], [5.0, 13.0], [10.0, 30.0]
+    z4 = [-40.0, -10.0, 15.0, 40.0]
+    lerp = lambda r, zz: r[0] + (zz + 40.0) / 80.0 * (r[1] - r[0])  # noqa: E731
+    rn4 = [lerp(rn2, zz) for zz in z4]
+    rx4 = [lerp(rx2, zz) for zz in z4]
+    a = oracle.Solid("polycone", z2, rn2, rx2, 0.3, 4.0)
+    b = oracle.Solid("polycone", z4, rn4, rx4, 0.3, 4.0)
+    spec = {"kind": "polycone", "params": (tuple(z2), tuple(rn2), tuple(rx2), 0.3, 4.0)}
+    t = W.tracks_for_solid(spec, 20000, seed=6)
+    # and points exactly on the internal planes, well inside radially
+    g = np.random.default_rng(6)
+    m = 2000
+    zi = np.where(g.random(m) < 0.5, -10.0, 15.0)
+    rr = np.array([g.uniform(lerp(rn2, q) + 0.5, lerp(rx2, q) - 0.5) for q in zi])
+    ph = 0.3 + g.uniform(0.1, 3.9, m)
+    for k, v in zip("x y z".split(), (rr * np.cos(ph), rr * np.sin(ph), zi)):
+        t[k] = np.concatenate([t[k], v])
+    dd = W.isotropic(m, g)
+    for i, k in enumerate(("dx", "dy", "dz")):
+        t[k] = np.concatenate([t[k], dd[:, i]])
+    ra, rb = a.query(**t), b.query(**t)
+    assert (rb["inside"][-m:] == IN).all()
+    s = np.array([a.s_code([t["x"][i], t["y"][i], t["z"][i]]) for i in range(len(t["x"]))])
+    ok = _away_from_band(s)
+    assert (ra["inside"][ok] == rb["inside"][ok]).all()
+    for k in ("dist_in", "dist_out"):
+        fin = np.isfinite(ra[k]) & ok
+        assert np.allclose(ra[k][fin], rb[k][fin], rtol=1e-9, atol=1e-9), k
+
+
+# ------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("idx", range(len(ALL_SPECS)))
+def test_returned_distance_lands_on_surface(idx):
+    spec = ALL_SPECS[idx]
+    s = sol(spec)
+    t = W.tracks_for_solid(spec, 4000, seed=100 + idx)
+    r = s.query(**t)
+    P = np.stack([t["x"], t["y"], t["z"]], 1)
+    D = np.stack([t["dx"], t["dy"], t["dz"]], 1)
+    for k in ("dist_in", "dist_out"):
+        v = r[k]
+        m = np.isfinite(v) & (v > 0)
+        q = P[m] + v[m, None] * D[m]
+        codes = s.inside(q)
+        assert (codes == SURF).all(), (spec["kind"], k, np.bincount(codes, minlength=3))
+    # zero distances only from the surface, -1 only from the wrong side
+    assert (r["inside"][r["dist_in"] == 0] == SURF).all()
+    assert (r["inside"][r["dist_out"] == 0] == SURF).all()
+    assert ((r["dist_in"] == -1) == (r["inside"] == IN)).all()
+    assert ((r["dist_out"] == -1) == (r["inside"] == OUT)).all()
+    assert np.isfinite(r["dist_out"]).all()
+    for k in r:
+        if k != "inside":
+            assert not np.isnan(r[k]).any()
+
+
+@pytest.mark.parametrize("idx", range(len(ALL_SPECS)))
+def test_safety_is_a_lower_bound(idx):
+    """0 <= safety <= every distance along any direction (here: the track's own
+    direction and 64 Fibonacci directions)."""
+    spec = ALL_SPECS[idx]
+    s = sol(spec)
+    n = 600
+    t = W.tracks_for_solid(spec, n, seed=200 + idx)
+    r = s.query(**t)
+    k = np.arange(64) + 0.5
+    th = np.arccos(1 - 2 * k / 64)
+    ph = math.pi * (1 + 5 ** 0.5) * k
+    fib = np.stack([np.cos(ph) * np.sin(th), np.sin(ph) * np.sin(th), np.cos(th)], 1)
+    rep = lambda a: np.repeat(a, 64)  # noqa: E731
+    tt = {"x": rep(t["x"]), "y": rep(t["y"]), "z": rep(t["z"]),
+          "dx": np.tile(fib[:, 0], n), "dy": np.tile(fib[:, 1], n), "dz": np.tile(fib[:, 2], n)}
+    rr = s.query(**tt)
+    din = rr["dist_in"].reshape(n, 64)
+    dout = rr["dist_out"].reshape(n, 64)
+    out = r["inside"] == OUT
+    ins = r["inside"] == IN
+    assert (r["safety_in"][out] > H).all()
+    assert (r["safety_out"][ins] > H).all()
+    assert (r["safety_in"][out] <= din[out].min(axis=1) + 1e-9).all()
+    assert (r["safety_in"][out] <= np.where(r["dist_in"][out] >= 0, r["dist_in"][out], np.inf) + 1e-9).all()
+    assert (r["safety_out"][ins] <= dout[ins].min(axis=1) + 1e-9).all()
+    assert (r["safety_out"][ins] <= r["dist_out"][ins] + 1e-9).all()
+
+
+def test_safety_exact_for_full_tube_interior():
+    t = oracle.Solid("tube", 5.0, 20.0, 30.0, 0.0, 2 * math.pi)
+    g = np.random.default_rng(9)
+    n = 5000
+    rr = np.sqrt(g.uniform(26, 399, n))
+    ph = g.uniform(0, 2 * math.pi, n)
+    z = g.uniform(-29, 29, n)
+    r = t.query(rr * np.cos(ph), rr * np.sin(ph), z, want=("safety_out",))
+    want = np.minimum(np.minimum(20 - rr, rr - 5), 30 - np.abs(z))
+    assert np.allclose(r["safety_out"], want, atol=1e-12)
+
+
+# -------------------------------------------------------- brute force
+
+def _march(s, P, D, want_inside, tmax, step):
+    """First t > 0 at which the (coarsely sampled, then bisected) ray crosses to the
+    wanted side of the solid, judged by the sign of s with no tolerance."""
+    n = len(P)
+    found = np.full(n, np.inf)
+    lo = np.zeros(n)
+    active = np.ones(n, bool)
+    ts = np.arange(step, tmax + step, step)
+    for tcur in ts:
+        idx = np.nonzero(active)[0]
+        if len(idx) == 0:
+            break
+        q = P[idx] + tcur * D[idx]
+        v = s.s_values(q)
+        hit = (v <= 0) if want_inside else (v > 0)
+        hi_idx = idx[hit]
+        found[hi_idx] = tcur
+        active[hi_idx] = False
+        lo[idx[~hit]] = tcur
+    m = np.isfinite(found)
+    a, b = lo[m].copy(), found[m].copy()
+    Pm, Dm = P[m], D[m]
+    for _ in range(50):
+        mid = 0.5 * (a + b)
+        v = s.s_values(Pm + mid[:, None] * Dm)
+        hit = (v <= 0) if want_inside else (v > 0)
+        b = np.where(hit, mid, b)
+        a = np.where(hit, a, mid)
+    found[m] = b
+    return found
+
+
+@pytest.mark.parametrize("idx", [0, 1, 2, 3, 4, 5, 7, 8, 9, 10])
+def test_brute_force_ray_march(idx):
+    spec = ALL_SPECS[idx]
+    s = sol(spec)
+    n = 300
+    t = W.tracks_for_solid(spec, n, seed=300 + idx, near_frac=0.0)
+    P = np.stack([t["x"], t["y"], t["z"]], 1)
+    D = np.stack([t["dx"], t["dy"], t["dz"]], 1)
+    r = s.query(**t)
+    hb = W.bounding_half(spec)
+    tmax = 2.0 * np.linalg.norm(hb * 2.0 + 1.0)
+    step = float(max(hb.min() / 200.0, 0.01))
+    out = r["inside"] == OUT
+    ins = r["inside"] == IN
+    te = _march(s, P[out], D[out], True, tmax, step)
+    tx = _march(s, P[ins], D[ins], False, tmax, step)
+    got_e, got_x = r["dist_in"][out], r["dist_out"][ins]
+    # the oracle is never later than the march (a thin chord can hide from the march)
+    fin = np.isfinite(te)
+    assert (got_e[fin] <= te[fin] + 1e-9).all()
+    with np.errstate(invalid="ignore"):
+        agree_e = np.where(fin, np.abs(got_e - te) <= 1e-9, np.isinf(got_e))
+    agree_x = np.abs(got_x - tx) <= 1e-9
+    assert agree_e.mean() >= 0.985, agree_e.mean()
+    assert agree_x.mean() >= 0.985, agree_x.mean()
+
+
+# ------------------------------------------------------------- golden
+
+def test_golden_analytic_cases():
+    with open(os.path.join(GOLDEN, "analytic_cases.json")) as f:
+        cases = json.load(f)["cases"]
+    assert len(cases) >= 20
+    for c in cases:
+        s = oracle.Solid(c["kind"], *c["params"])
+        p, d = c["p"], c["d"]
+        r = s.query([p[0]], [p[1]], [p[2]], [d[0]], [d[1]], [d[2]])
+        for k, v in c["expect"].items():
+            got = r[k][0]
+            want = eval(str(v), {"__builtins__": {}}, {"sqrt": math.sqrt, "inf": math.inf, "atan": math.atan})
+            if math.isinf(want):
+                assert np.isinf(got) and got > 0, (c["name"], k, got)
+            else:
+                assert got == pytest.approx(want, abs=1e-12), (c["name"], k, got, want)
+
+
+# ------------------------------------------------------------ navigation
+
+def _nested():
+    g = W.nested_geometry()
+    return g, oracle.Geometry(g["solids"], g["nodes"])
+
+
+def test_locate_by_construction():
+    g, geo = _nested()
+    nodes = g["nodes"]
+    # cell centres are in their cell; shell mid-radius points between cells are in the shell
+    cell_ids = [i for i, nd in enumerate(nodes) if nd["solid"] == 1]
+    c = np.array([nodes[i]["t"] for i in cell_ids])
+    assert (geo.locate(c[:, 0], c[:, 1], c[:, 2]) == np.array(cell_ids)).all()
+    shells = [i for i, nd in enumerate(nodes) if nd["parent"] == 0]
+    rmid = np.array([g["solids"][nodes[i]["solid"]]["params"][0] + 9.0 for i in shells])
+    z = np.zeros_like(rmid)
+    assert (geo.locate(rmid, z, z) == np.array(shells)).all()       # phi = 0: between cells
+    assert (geo.locate(rmid * 0 + 9.5, z, z) == 0).all()           # gap inside the first shell
+    assert (geo.locate(np.array([300.0, 0.0]), np.array([0.0, 0.0]), np.array([0.0, 600.0])) == -1).all()
+
+
+def test_nav_step_radial_closed_form():
+    """A track in a shell at azimuth 0 (between cells) moving radially outwards leaves
+    through the shell's outer wall: step = rmax - r, next = -1; safety = min(distance
+    to the walls, distance to the nearest cell)."""
+    g, geo = _nested()
+    nodes = g["nodes"]
+    shells = [i for i, nd in enumerate(nodes) if nd["parent"] == 0]
+    n = len(shells)
+    rmin = np.array([g["solids"][nodes[i]["solid"]]["params"][0] for i in shells])
+    r0 = rmin + 2.0
+    z = np.full(n, 7.0)
+    one, zero = np.ones(n), np.zeros(n)
+    res = geo.nav_step(r0, zero, z, one, zero, zero, np.array(shells, np.int32))
+    assert np.allclose(res["step"], rmin + 18.0 - r0, atol=1e-12)
+    assert (res["next"] == -1).all()
+    assert (res["safety"] >= 0).all() and (res["safety"] <= 2.0 + 1e-12).all()
+
+
+def test_nav_step_brute_force_tree():
+    """The navigation step equals the minimum over the mother's exit and every daughter's
+    entry, computed here with explicit frame changes and the per-solid queries."""
+    g, geo = _nested()
+    nodes = g["nodes"]
+    t = W.nested_tracks(3000, seed=1, geom=g)
+    node = geo.locate(t["x"], t["y"], t["z"])
+    keep = node >= 0
+    for k in t:
+        t[k] = t[k][keep]
+    node = node[keep]
+    res = geo.nav_step(t["x"], t["y"], t["z"], t["dx"], t["dy"], t["dz"], node)
+    solids = [oracle.Solid.from_spec(s) for s in g["solids"]]
+    # global placement by explicit composition along the parent chain
+    Rg, tg = [], []
+    for i, nd in enumerate(nodes):
+        R, tt = np.asarray(nd["R"], float), np.asarray(nd["t"], float)
+        if nd["parent"] >= 0:
+            R, tt = Rg[nd["parent"]] @ R, Rg[nd["parent"]] @ tt + tg[nd["parent"]]
+        Rg.append(R); tg.append(tt)
+    P = np.stack([t["x"], t["y"], t["z"]], 1)
+    D = np.stack([t["dx"], t["dy"], t["dz"]], 1)
+    for i in range(0, len(node), 7):
+        v = node[i]
+        pl, dl = Rg[v].T @ (P[i] - tg[v]), Rg[v].T @ D[i]
+        rm = solids[nodes[v]["solid"]].query([pl[0]], [pl[1]], [pl[2]], [dl[0]], [dl[1]], [dl[2]])
+        cands = [(rm["dist_out"][0], -1)]
+        saf = [rm["safety_out"][0]]
+        for c in range(len(nodes)):
+            if nodes[c]["parent"] != v:
+                continue
+            pc, dc = Rg[c].T @ (P[i] - tg[c]), Rg[c].T @ D[i]
+            rc = solids[nodes[c]["solid"]].query([pc[0]], [pc[1]], [pc[2]], [dc[0]], [dc[1]], [dc[2]])
+            if rc["dist_in"][0] >= 0:
+                cands.append((rc["dist_in"][0], c))
+            if rc["safety_in"][0] >= 0:
+                saf.append(rc["safety_in"][0])
+        best = min(cands, key=lambda tc: (tc[0], 0 if tc[1] >= 0 else 1, tc[1]))
+        assert res["step"][i] == pytest.approx(best[0], abs=1e-9)
+        assert res["next"][i] == best[1]
+        assert res["safety"][i] == pytest.approx(min(saf), abs=1e-9)

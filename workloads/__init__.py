@@ -1,0 +1,372 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module only draws random numbers: solid descriptions, point/direction
+baskets, basket tables and the nested detector layout.  It holds none of the
+query arithmetic (no inside test, no distance, no safety); points are placed by
+sampling each solid's parametric description (its faces, its radial and
+azimuthal ranges), and a point "near a surface" is a sampled surface point moved
+by an isotropic offset no longer than the stated band.
+
+Workloads (random points and isotropic directions, as in the paper's speed test
+of the VecGeom section, where random particles are tested against a Box and a
+Tube):
+
+* ``box1024``     -- box (10,20,30) mm, 1024 tracks uniform in a (20,40,60) mm world
+                     box, 5% of them within 1e-10 mm of a face.
+* ``tube_cone_1m``-- tube segment (5,20,30, phi 0-270 deg) and cone segment
+                     (0,10,5,25,40, full phi), 2^20 tracks each, half sampled
+                     inside the solid and half uniform in a world box twice the
+                     bounding box, 10% within 1e-8 mm of a surface.
+* ``precision_16m``-- 2^24 tracks per solid over box, trd (10,20,15,5,30), tube,
+                     cone and an 8-plane polycone, same recipe.
+* ``batched``     -- 4096 baskets, sizes log-uniform in [16, 4096], each against one
+                     of 64 solids of the six types with parameters in 1-100 mm.
+* ``nested``      -- world box holding 10 concentric tube shells holding 32 box
+                     cells each; requests with sizes log-uniform in [1, 65536].
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 1512_06637
+TWO_PI = 2.0 * math.pi
+DEG = math.pi / 180.0
+
+# ----------------------------------------------------------------- solids
+
+BOX_M1 = {"kind": "box", "params": (10.0, 20.0, 30.0)}
+TUBE_M2 = {"kind": "tube", "params": (5.0, 20.0, 30.0, 0.0, 270.0 * DEG)}
+CONE_M2 = {"kind": "cone", "params": (0.0, 10.0, 5.0, 25.0, 40.0, 0.0, TWO_PI)}
+TRD_M3 = {"kind": "trd", "params": (10.0, 20.0, 15.0, 5.0, 30.0)}
+
+
+def rng(tag: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + int(tag)))
+
+
+def polycone_m3(seed: int = 2, nz: int = 8) -> dict:
+    """8 z-planes sorted in [-50, 50] at least 2 mm apart, 1 <= rmin < rmax <= 50, full phi."""
+    g = rng(1000 + seed)
+    u = np.sort(g.uniform(0.0, 100.0 - 2.0 * (nz - 1), nz))
+    z = -50.0 + u + 2.0 * np.arange(nz)
+    rmin = g.uniform(1.0, 40.0, nz)
+    rmax = np.minimum(50.0, rmin + g.uniform(2.0, 30.0, nz))
+    return {"kind": "polycone", "params": (tuple(z), tuple(rmin), tuple(rmax), 0.0, TWO_PI)}
+
+
+def trap_random(g: np.random.Generator, lo=1.0, hi=100.0) -> dict:
+    """A planar trapezoid: the +dz face is k times the -dz face (k in [0.5, 1.5]) so
+    that paired edges stay parallel; theta, phi in [0, 15] deg, alpha1 = alpha2."""
+    dz = g.uniform(lo, hi)
+    dy1 = g.uniform(lo, hi / 1.5)
+    dx1 = g.uniform(lo, hi / 1.5)
+    dx2 = g.uniform(lo, hi / 1.5)
+    k = g.uniform(0.5, 1.5)
+    th = g.uniform(0, 15) * DEG
+    ph = g.uniform(0, 15) * DEG
+    al = g.uniform(-15, 15) * DEG
+    return {"kind": "trap", "params": ((dz, th, ph, dy1, dx1, dx2, al, k * dy1, k * dx1, k * dx2, al),)}
+
+
+def random_solid(kind: str, g: np.random.Generator, lo=1.0, hi=100.0) -> dict:
+    """One solid of the given kind with seeded parameters in [lo, hi] mm."""
+    u = lambda a=lo, b=hi: float(g.uniform(a, b))  # noqa: E731
+    if kind == "box":
+        return {"kind": "box", "params": (u(), u(), u())}
+    if kind == "trd":
+        return {"kind": "trd", "params": (u(), u(), u(), u(), u())}
+    if kind == "trap":
+        return trap_random(g, lo, hi)
+    phi_choice = g.integers(0, 3)
+    if phi_choice == 0:
+        sphi, dphi = 0.0, TWO_PI
+    else:
+        sphi = float(g.uniform(0, 360)) * DEG
+        dphi = float(g.uniform(30, 330)) * DEG
+    if kind == "tube":
+        rmax = u(lo + 1.0, hi)
+        rmin = float(g.uniform(0, rmax - 0.5)) if g.integers(0, 4) else 0.0
+        return {"kind": "tube", "params": (rmin, rmax, u(), sphi, dphi)}
+    if kind == "cone":
+        rmax1, rmax2 = u(lo + 1.0, hi), u(lo + 1.0, hi)
+        rmin1 = float(g.uniform(0, rmax1 - 0.5)) if g.integers(0, 3) else 0.0
+        rmin2 = float(g.uniform(0, rmax2 - 0.5)) if g.integers(0, 3) else 0.0
+        return {"kind": "cone", "params": (rmin1, rmax1, rmin2, rmax2, u(), sphi, dphi)}
+    if kind == "polycone":
+        nz = int(g.integers(2, 9))
+        span = u(10.0, hi)
+        z = np.sort(g.uniform(-span, span, nz))
+        z = z + 0.5 * np.arange(nz)  # strictly increasing
+        rmin = g.uniform(0.0, 0.5 * hi, nz) * (g.random(nz) < 0.7)
+        rmax = rmin + g.uniform(lo, 0.5 * hi, nz)
+        return {"kind": "polycone", "params": (tuple(z), tuple(rmin), tuple(rmax), sphi, dphi)}
+    raise ValueError(kind)
+
+
+KINDS6 = ("box", "trd", "trap", "tube", "cone", "polycone")
+
+
+def solid_table(n: int = 64, seed: int = 3) -> list[dict]:
+    """n solids of the six types in turn (type i % 6), seeded parameters in 1-100 mm."""
+    g = rng(2000 + seed)
+    return [random_solid(KINDS6[i % 6], g) for i in range(n)]
+
+
+# ------------------------------------------------- parametric descriptions
+
+def _trap_vertices(p):
+    dz, th, ph, dy1, dx1, dx2, a1, dy2, dx3, dx4, a2 = p
+    out = []
+    for zf, dy, dxa, dxb, al in ((-dz, dy1, dx1, dx2, a1), (dz, dy2, dx3, dx4, a2)):
+        cx = zf * math.tan(th) * math.cos(ph)
+        cy = zf * math.tan(th) * math.sin(ph)
+        sh = dy * math.tan(al)
+        out += [(cx - sh - dxa, cy - dy, zf), (cx - sh + dxa, cy - dy, zf),
+                (cx + sh - dxb, cy + dy, zf), (cx + sh + dxb, cy + dy, zf)]
+    return np.array(out)
+
+
+def _as_trap(spec):
+    k, p = spec["kind"], spec["params"]
+    if k == "box":
+        dx, dy, dz = p
+        return (dz, 0, 0, dy, dx, dx, 0, dy, dx, dx, 0)
+    if k == "trd":
+        dx1, dx2, dy1, dy2, dz = p
+        return (dz, 0, 0, dy1, dx1, dx1, 0, dy2, dx2, dx2, 0)
+    return tuple(p[0])
+
+
+def _as_pcon(spec):
+    k, p = spec["kind"], spec["params"]
+    if k == "tube":
+        rmin, rmax, dz, sphi, dphi = p
+        return [-dz, dz], [rmin, rmin], [rmax, rmax], sphi, dphi
+    if k == "cone":
+        rmin1, rmax1, rmin2, rmax2, dz, sphi, dphi = p
+        return [-dz, dz], [rmin1, rmin2], [rmax1, rmax2], sphi, dphi
+    z, rmin, rmax, sphi, dphi = p
+    return list(z), list(rmin), list(rmax), sphi, dphi
+
+
+def bounding_half(spec) -> np.ndarray:
+    """Half-lengths of an axis-aligned box around the origin that holds the solid."""
+    if spec["kind"] in ("box", "trd", "trap"):
+        v = _trap_vertices(_as_trap(spec))
+        return np.abs(v).max(axis=0)
+    z, rmin, rmax, _, _ = _as_pcon(spec)
+    r = max(rmax)
+    return np.array([r, r, max(abs(z[0]), abs(z[-1]))])
+
+
+def _sample_inside(spec, n, g):
+    """Points drawn from the solid's parametric interior (not uniform in volume)."""
+    if spec["kind"] in ("box", "trd", "trap"):
+        v = _trap_vertices(_as_trap(spec))
+        a, b, c = g.random(n), g.random(n), g.random(n)
+        # trilinear blend of the 8 vertices: v[4j + 2i + k] at (k = x-side, i = y-side, j = z-side)
+        w = np.empty((n, 8))
+        for j in range(2):
+            for i in range(2):
+                for k in range(2):
+                    w[:, 4 * j + 2 * i + k] = (c if j else 1 - c) * (b if i else 1 - b) * (a if k else 1 - a)
+        return w @ v
+    z, rmin, rmax, sphi, dphi = _as_pcon(spec)
+    z, rmin, rmax = map(np.asarray, (z, rmin, rmax))
+    zz = g.uniform(z[0], z[-1], n)
+    k = np.clip(np.searchsorted(z, zz, side="right") - 1, 0, len(z) - 2)
+    f = (zz - z[k]) / (z[k + 1] - z[k])
+    r0 = rmin[k] + f * (rmin[k + 1] - rmin[k])
+    r1 = rmax[k] + f * (rmax[k + 1] - rmax[k])
+    rr = np.sqrt(g.uniform(r0 * r0, r1 * r1))
+    ph = sphi + g.random(n) * min(dphi, TWO_PI)
+    return np.stack([rr * np.cos(ph), rr * np.sin(ph), zz], axis=1)
+
+
+def _sample_surface(spec, n, g):
+    """Points drawn on the solid's faces, face chosen with probability ~ its area."""
+    if spec["kind"] in ("box", "trd", "trap"):
+        v = _trap_vertices(_as_trap(spec))
+        quads = [(0, 1, 3, 2), (4, 5, 7, 6), (0, 1, 5, 4), (2, 3, 7, 6), (0, 2, 6, 4), (1, 3, 7, 5)]
+        areas = []
+        for q in quads:
+            A, B, C, D = v[list(q)]
+            areas.append(0.5 * np.linalg.norm(np.cross(C - A, D - B)))
+        areas = np.array(areas)
+        f = g.choice(6, size=n, p=areas / areas.sum())
+        a, b = g.random(n), g.random(n)
+        out = np.empty((n, 3))
+        for fi, q in enumerate(quads):
+            m = f == fi
+            A, B, C, D = v[list(q)]
+            aa, bb = a[m, None], b[m, None]
+            out[m] = (1 - aa) * (1 - bb) * A + aa * (1 - bb) * B + aa * bb * C + (1 - aa) * bb * D
+        return out
+    z, rmin, rmax, sphi, dphi = _as_pcon(spec)
+    z, rmin, rmax = map(np.asarray, (z, rmin, rmax))
+    dp = min(dphi, TWO_PI)
+    has_phi = dphi < TWO_PI
+    # faces: lateral outer/inner per section, two end caps, two phi planes
+    faces, areas = [], []
+    for k in range(len(z) - 1):
+        h = z[k + 1] - z[k]
+        for side, rr in (("out", rmax), ("in", rmin)):
+            slant = math.hypot(h, rr[k + 1] - rr[k])
+            a = 0.5 * (rr[k] + rr[k + 1]) * dp * slant
+            if a > 0:
+                faces.append((side, k)); areas.append(a)
+    for j in (0, len(z) - 1):
+        faces.append(("cap", j)); areas.append(0.5 * dp * (rmax[j] ** 2 - rmin[j] ** 2))
+    if has_phi:
+        prof = sum((z[k + 1] - z[k]) * 0.5 * ((rmax[k] - rmin[k]) + (rmax[k + 1] - rmin[k + 1]))
+                   for k in range(len(z) - 1))
+        faces += [("phi", 0), ("phi", 1)]; areas += [prof, prof]
+    areas = np.array(areas)
+    f = g.choice(len(faces), size=n, p=areas / areas.sum())
+    out = np.empty((n, 3))
+    u, w = g.random(n), g.random(n)
+    for fi, (kind, k) in enumerate(faces):
+        m = f == fi
+        cnt = int(m.sum())
+        if cnt == 0:
+            continue
+        ph = sphi + u[m] * dp
+        if kind in ("out", "in"):
+            rr = rmax if kind == "out" else rmin
+            zz = z[k] + w[m] * (z[k + 1] - z[k])
+            r = rr[k] + (zz - z[k]) / (z[k + 1] - z[k]) * (rr[k + 1] - rr[k])
+        elif kind == "cap":
+            zz = np.full(cnt, z[k])
+            r = np.sqrt(rmin[k] ** 2 + w[m] * (rmax[k] ** 2 - rmin[k] ** 2))
+        else:
+            ph = np.full(cnt, sphi + (dp if k else 0.0))
+            sec = np.clip(np.searchsorted(z, z[0] + w[m] * (z[-1] - z[0]), side="right") - 1, 0, len(z) - 2)
+            zz = z[0] + w[m] * (z[-1] - z[0])
+            fr = (zz - z[sec]) / (z[sec + 1] - z[sec])
+            r0 = rmin[sec] + fr * (rmin[sec + 1] - rmin[sec])
+            r1 = rmax[sec] + fr * (rmax[sec + 1] - rmax[sec])
+            r = r0 + g.random(cnt) * (r1 - r0)
+        out[m] = np.stack([r * np.cos(ph), r * np.sin(ph), zz], axis=1)
+    return out
+
+
+def isotropic(n: int, g: np.random.Generator) -> np.ndarray:
+    v = g.standard_normal((n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _offset(n, band, g):
+    return isotropic(n, g) * g.uniform(0.0, band, (n, 1))
+
+
+def tracks_for_solid(spec: dict, n: int, seed: int, near_frac=0.10, band=1e-8,
+                     inside_frac=0.5, world_scale=2.0) -> dict:
+    """Half (inside_frac) parametric interior points, the rest uniform in a world box
+    world_scale times the bounding box; near_frac of all points moved onto a surface
+    point plus an isotropic offset of length <= band.  Directions are isotropic."""
+    g = rng(seed)
+    hb = bounding_half(spec) * world_scale + 1.0
+    n_in = int(round(n * inside_frac))
+    pts = np.empty((n, 3))
+    pts[:n_in] = _sample_inside(spec, n_in, g)
+    pts[n_in:] = g.uniform(-1, 1, (n - n_in, 3)) * hb
+    n_near = int(round(n * near_frac))
+    if n_near:
+        idx = g.choice(n, n_near, replace=False)
+        pts[idx] = _sample_surface(spec, n_near, g) + _offset(n_near, band, g)
+    perm = g.permutation(n)
+    pts = pts[perm]
+    d = isotropic(n, g)
+    return soa(pts, d)
+
+
+def soa(pts, d) -> dict:
+    pts = np.asarray(pts, np.float64)
+    d = np.asarray(d, np.float64)
+    return {"x": np.ascontiguousarray(pts[:, 0]), "y": np.ascontiguousarray(pts[:, 1]),
+            "z": np.ascontiguousarray(pts[:, 2]), "dx": np.ascontiguousarray(d[:, 0]),
+            "dy": np.ascontiguousarray(d[:, 1]), "dz": np.ascontiguousarray(d[:, 2])}
+
+
+def box1024(n: int = 1024, seed: int = 0) -> dict:
+    """Box (10,20,30): points uniform in a (20,40,60) world box, 5% within 1e-10 mm of a face."""
+    g = rng(seed)
+    D = np.array(BOX_M1["params"])
+    pts = g.uniform(-1, 1, (n, 3)) * (2 * D)
+    n_face = int(round(0.05 * n))
+    idx = g.choice(n, n_face, replace=False)
+    axis = g.integers(0, 3, n_face)
+    sign = np.where(g.random(n_face) < 0.5, -1.0, 1.0)
+    face_pts = g.uniform(-1, 1, (n_face, 3)) * D
+    face_pts[np.arange(n_face), axis] = sign * D[axis] + g.uniform(-1e-10, 1e-10, n_face)
+    pts[idx] = face_pts
+    return soa(pts, isotropic(n, g))
+
+
+# --------------------------------------------------------- batched form
+
+def batched(n_baskets: int = 4096, seed: int = 4, lo: int = 16, hi: int = 4096,
+            n_solids: int = 64) -> dict:
+    """Basket table {offset, n, solid} with log-uniform sizes and the tracks of every
+    basket drawn for its own solid; returns solids, baskets and one SoA of all tracks."""
+    g = rng(3000 + seed)
+    solids = solid_table(n_solids, seed)
+    sizes = np.floor(np.exp(g.uniform(math.log(lo), math.log(hi), n_baskets))).astype(np.int64)
+    sizes = np.clip(sizes, lo, hi)
+    sid = g.integers(0, n_solids, n_baskets).astype(np.int32)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    total = int(sizes.sum())
+    cols = {k: np.empty(total) for k in ("x", "y", "z", "dx", "dy", "dz")}
+    for b in range(n_baskets):
+        t = tracks_for_solid(solids[sid[b]], int(sizes[b]), seed=10_000 + 7919 * seed + b)
+        o = offs[b]
+        for k in cols:
+            cols[k][o:o + sizes[b]] = t[k]
+    return {"solids": solids, "offset": offs, "n": sizes, "solid": sid, "tracks": cols}
+
+
+# ------------------------------------------------------ nested geometry
+
+def nested_geometry(n_shells: int = 10, cells_phi: int = 8, cells_z: int = 4) -> dict:
+    """World box (250,250,550) mm holding 10 tube shells (rmin = 10 + 19k, rmax = rmin + 18,
+    dz = 500, full phi), each holding 32 box cells (4.5, 4.5, 112.5) centred at the shell's
+    mid radius, 8 in phi (22.5 + 45 j deg, rotated about z) by 4 in z (-375, -125, 125, 375)."""
+    solids = [{"kind": "box", "params": (250.0, 250.0, 550.0)},
+              {"kind": "box", "params": (4.5, 4.5, 112.5)}]
+    ident = np.eye(3)
+    nodes = [{"solid": 0, "parent": -1, "R": ident, "t": np.zeros(3)}]
+    shell_nodes = []
+    for k in range(n_shells):
+        rmin = 10.0 + 19.0 * k
+        solids.append({"kind": "tube", "params": (rmin, rmin + 18.0, 500.0, 0.0, TWO_PI)})
+        nodes.append({"solid": len(solids) - 1, "parent": 0, "R": ident, "t": np.zeros(3)})
+        shell_nodes.append(len(nodes) - 1)
+    for k, sn in enumerate(shell_nodes):
+        rmid = 10.0 + 19.0 * k + 9.0
+        for iz, zc in enumerate((-375.0, -125.0, 125.0, 375.0)[:cells_z]):
+            for j in range(cells_phi):
+                ph = (22.5 + 45.0 * j) * DEG
+                c, s = math.cos(ph), math.sin(ph)
+                R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+                nodes.append({"solid": 1, "parent": sn, "R": R, "t": np.array([rmid * c, rmid * s, zc])})
+    return {"solids": solids, "nodes": nodes}
+
+
+def nested_tracks(n: int, seed: int, geom: dict | None = None) -> dict:
+    """Points uniform in the world box, isotropic directions."""
+    g = rng(4000 + seed)
+    hb = np.array((geom or nested_geometry())["solids"][0]["params"])
+    pts = g.uniform(-1, 1, (n, 3)) * hb
+    return soa(pts, isotropic(n, g))
+
+
+def request_sizes(n_req: int, seed: int, lo: int = 1, hi: int = 65536) -> np.ndarray:
+    g = rng(5000 + seed)
+    return np.clip(np.floor(np.exp(g.uniform(math.log(lo), math.log(hi), n_req))), lo, hi).astype(np.int64)
+
+
+def poisson_arrivals(n_req: int, rate_per_s: float, seed: int) -> np.ndarray:
+    g = rng(6000 + seed)
+    return np.cumsum(g.exponential(1.0 / rate_per_s, n_req))
