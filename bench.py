@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: track-solid queries per second on the precision-form workload.
+
+One step = all five queries (Inside, DistanceToIn, DistanceToOut, SafetyToIn,
+SafetyToOut) for 2^24 tracks against each of five solids (box 10x20x30, trd
+(10,20,15,5,30), tube segment (5,20,30, phi 0-270 deg), cone segment
+(0,10,5,25,40), an 8-plane polycone), i.e. 5 * 2^24 tracks and 25 * 2^24
+queries, inputs resident in HBM.  Synthetic, seeded inputs (half inside each
+solid, 10% within 1e-8 mm of a surface, isotropic directions).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same workload, on the host cores.
+
+Multi-GPU (torchrun): every rank runs its own copy of the workload (the tracks
+are independent; no data-path collective) -> weak scaling; the time is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+N_QUERIES = 5
+BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 doubles out
+
+
+def specs():
+    return [("box", W.BOX_M1), ("trd", W.TRD_M3), ("tube", W.TUBE_M2), ("cone", W.CONE_M2),
+            ("polycone", W.polycone_m3())]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32_refine"])
+    ap.add_argument("--tracks", type=int, default=1 << 24, help="tracks per solid")
+    ap.add_argument("--cpu-sample", type=int, default=40000, help="tracks per solid for the oracle")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(tracks_per_solid: dict, sample: int):
+    """The oracle as it stands, on a bounded sample of each solid's tracks, all host cores."""
+    import oracle
+    threads = os.cpu_count() or 1
+    total_tracks = 0
+    t0 = time.perf_counter()
+    for name, spec in specs():
+        tr = {k: v[:sample] for k, v in tracks_per_solid[name].items()}
+        oracle.Solid.from_spec(spec).query(**tr, threads=threads)
+        total_tracks += len(tr["x"])
+    dt = time.perf_counter() - t0
+    return {"value": total_tracks * N_QUERIES / dt, "unit": "queries/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"first {sample} tracks of each of the 5 solids' 2^24-track baskets, all five queries"}
+
+
+def gen_inputs(n: int):
+    return {name: W.tracks_for_solid(spec, n, seed=2) for name, spec in specs()}
+
+
+# ------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = args.cpu_sample
+    inputs = {name: W.tracks_for_solid(spec, sample, seed=2) for name, spec in specs()}
+    for _ in range(args.warmup):
+        cpu_baseline(inputs, sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cb = cpu_baseline(inputs, sample)
+    dt = time.perf_counter() - t0
+    value = args.steps * 5 * sample * N_QUERIES / dt
+    line = {"metric": "track-solid queries/s", "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "precision form: box, trd, tube, cone, polycone; 2^24 tracks per solid "
+                                   "(oracle step = bounded sample)", "tracks_per_solid_sampled": sample},
+            "cpu_baseline": {**cb, "value": value},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+
+    import paper_1512_06637_gb300 as gv
+    from paper_1512_06637_gb300 import build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    n = args.tracks
+    # host inputs are generated before the first CUDA call
+    inputs = gen_inputs(n)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    precision = args.precision
+    if precision == "auto":
+        precision = "fp32_refine" if gv_supports_fp32(gv) else "fp64"
+    dev = {name: {k: torch.from_numpy(v).cuda() for k, v in tr.items()} for name, tr in inputs.items()}
+    solids = {name: gv.Solid.from_spec(spec) for name, spec in specs()}
+    outs = {name: gv.alloc_results(n, "cuda") for name in solids}
+    ws = gv.Workspace(n) if precision == "fp32_refine" else None
+    stream = torch.cuda.current_stream()
+    names = list(solids)
+    launches_per_query = 2 if precision == "fp32_refine" else 1
+
+    def step(events=None):
+        for i, name in enumerate(names):
+            if events is not None:
+                events[i][0].record(stream)
+            gv.query(solids[name], dev[name], precision=precision, out=outs[name], workspace=ws,
+                     stream=stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, barrier + synchronize on both sides, clocks sampled
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in names]
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    per_solid_ms = {name: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+                    for i, name in enumerate(names)}
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    queries = world * args.steps * len(names) * n * N_QUERIES
+    value = queries / (ms * 1e-3)
+
+    # dominant kernel: the query pass with the largest mean time per launch
+    dom = max(per_solid_ms, key=per_solid_ms.get)
+    dom_ms = per_solid_ms[dom]
+    peaks = load_peaks()
+    achieved = n * BYTES_PER_TRACK / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": f"query pass ({precision}) on {dom}", "peak_source": peaks["source"]}
+
+    refined = None
+    if ws is not None:
+        refined = {}
+        for name in names:
+            gv.query(solids[name], dev[name], precision=precision, out=outs[name], workspace=ws, stream=stream)
+            refined[name] = ws.refined(stream) / n
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(gv, torch, inputs, solids, precision, n, max(1, min(args.steps, 3)), world)
+
+    line = {
+        "metric": "track-solid queries/s", "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if precision == "fp32_refine" else "f64", "data": "synthetic",
+        "config": {"workload": "precision form: box, trd, tube, cone, polycone; 2^24 tracks per solid; "
+                               "all five queries", "tracks_per_solid": n, "precision": precision,
+                   "l2": "inputs larger than L2 (4 GB per step)", "parallelism": f"replicas x{world}"},
+        "per_solid_ms": per_solid_ms,
+        "roofline": roofline,
+        "clocks": ck,
+        "gpu_launches": args.steps * len(names) * launches_per_query,
+        "e2e": e2e,
+    }
+    if refined is not None:
+        line["refined_fraction"] = refined
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(inputs, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(gv, torch, inputs, solids, precision, n, steps, world):
+    """Same metric through the public call with host buffers: pinned host inputs copied in,
+    queries, results copied back, all inside the timed region."""
+    host_in = {name: {k: torch.from_numpy(v).pin_memory() for k, v in tr.items()} for name, tr in inputs.items()}
+    dev_in = {name: {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in tr} for name, tr in inputs.items()}
+    dev_out = {name: gv.alloc_results(n, "cuda") for name in solids}
+    host_out = {name: {k: torch.empty(n, dtype=v.dtype).pin_memory() for k, v in dev_out[name].items()}
+                for name in solids}
+    ws = gv.Workspace(n) if precision == "fp32_refine" else None
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for name in solids:
+            for k in host_in[name]:
+                dev_in[name][k].copy_(host_in[name][k], non_blocking=True)
+            gv.query(solids[name], dev_in[name], precision=precision, out=dev_out[name], workspace=ws,
+                     stream=stream)
+            for k in dev_out[name]:
+                host_out[name][k].copy_(dev_out[name][k], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    h2d = sum(t.numel() * t.element_size() for tr in host_in.values() for t in tr.values())
+    d2h = sum(t.numel() * t.element_size() for tr in host_out.values() for t in tr.values())
+    return {"value": world * steps * len(solids) * n * N_QUERIES / (ms * 1e-3), "unit": "queries/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def gv_supports_fp32(gv) -> bool:
+    return getattr(gv, "HAS_FP32_REFINE", False)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json, copy)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -21,9 +21,11 @@
  *   candidate; the gaps between consecutive candidates are classified inside or
  *   outside by the sign of s at their midpoint (no tolerance).
  *   DistanceToIn:  INSIDE -> -1; SURFACE and entering -> 0; otherwise the first
- *                  candidate after which the gap is inside; none -> +inf.
+ *                  candidate where an outside gap is followed by an inside one;
+ *                  none -> +inf.
  *   DistanceToOut: OUTSIDE -> -1; SURFACE and leaving -> 0; otherwise the first
- *                  candidate after which the gap is outside.
+ *                  candidate where an inside gap is followed by an outside one;
+ *                  none (a surface point whose ray never gets inside) -> 0.
  *   A SURFACE point is "leaving" when some constraint within the band
  *   (g_i >= -h) grows along d, and "entering" when every such constraint
  *   decreases along d.
@@ -386,8 +388,12 @@ double or_dist_in(const or_solid* s, const double p[3], const double d[3]) {
   }
   double t[MAXROOTS];
   const int m = candidates(s, p, d, t);
-  for (int j = 1; j <= m; j++)
-    if (gap_inside(s, p, d, t, m, j)) return t[j - 1];
+  int prev = gap_inside(s, p, d, t, m, 0);
+  for (int j = 1; j <= m; j++) {
+    const int cur = gap_inside(s, p, d, t, m, j);
+    if (cur && !prev) return t[j - 1];
+    prev = cur;
+  }
   return INFINITY;
 }
 
@@ -401,9 +407,14 @@ double or_dist_out(const or_solid* s, const double p[3], const double d[3]) {
   }
   double t[MAXROOTS];
   const int m = candidates(s, p, d, t);
-  for (int j = 1; j <= m; j++)
-    if (!gap_inside(s, p, d, t, m, j)) return t[j - 1];
-  return INFINITY; /* a bounded solid is always left: reaching here is a bug */
+  int prev = gap_inside(s, p, d, t, m, 0);
+  for (int j = 1; j <= m; j++) {
+    const int cur = gap_inside(s, p, d, t, m, j);
+    if (!cur && prev) return t[j - 1];
+    prev = cur;
+  }
+  /* never inside: a surface point whose ray stays out leaves at once */
+  return 0.0;
 }
 
 void or_query(const or_solid* s, int64_t n,

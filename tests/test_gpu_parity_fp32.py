@@ -1,0 +1,172 @@
+"""Parity of the FP32 bulk pass + FP64 refinement with the CPU oracle (C ABI).
+
+Codes bit-exact, distances and safeties within 1e-5 relative (1e-9 mm below
+1e-4 mm), sentinels exact; the same inputs as the FP64 parity tests, the full
+2^20-track tube and cone baskets, sampled 2^24-track baskets, edge cases, and
+the refined fraction reported per solid.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests.helpers import compare, to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+SPECS = {"box": W.BOX_M1, "trd": W.TRD_M3, "tube": W.TUBE_M2, "cone": W.CONE_M2,
+         "polycone": W.polycone_m3()}
+TABLE = W.solid_table(24, seed=11)
+
+
+@pytest.fixture(scope="module")
+def gv():
+    import torch  # noqa: F401
+    import paper_1512_06637_gb300 as gv
+    from paper_1512_06637_gb300 import build
+    build.build()
+    return gv
+
+
+def run32(gv, spec, tr):
+    import torch
+    s = gv.Solid.from_spec(spec)
+    dev = to_device(tr, torch)
+    ws = gv.Workspace(len(tr["x"]))
+    out = gv.query(s, dev, precision="fp32_refine", workspace=ws)
+    refined = ws.refined()
+    torch.cuda.synchronize()
+    return to_host(out), refined
+
+
+@pytest.mark.parametrize("name", list(SPECS))
+def test_fp32_parity_named(gv, name):
+    spec = SPECS[name]
+    n = (1 << 17) + 37
+    tr = W.tracks_for_solid(spec, n, seed=500 + len(name))
+    got, refined = run32(gv, spec, tr)
+    want = oracle.Solid.from_spec(spec).query(**tr)
+    stats = compare(got, want, "fp32", name)
+    frac = refined / n
+    print(f"{name}: refined fraction {frac:.4f}; {stats}")
+    assert frac < 0.2
+
+
+@pytest.mark.parametrize("i", range(len(TABLE)))
+def test_fp32_parity_random_solids(gv, i):
+    spec = TABLE[i]
+    tr = W.tracks_for_solid(spec, 20011, seed=600 + i)
+    got, refined = run32(gv, spec, tr)
+    want = oracle.Solid.from_spec(spec).query(**tr)
+    compare(got, want, "fp32", f"{spec['kind']}#{i}")
+
+
+def test_fp32_box1024(gv):
+    tr = W.box1024()
+    got, _ = run32(gv, W.BOX_M1, tr)
+    want = oracle.Solid.from_spec(W.BOX_M1).query(**tr)
+    compare(got, want, "fp32", "box1024")
+
+
+@pytest.mark.parametrize("name", ["tube", "cone"])
+def test_fp32_full_1m(gv, name):
+    tr = W.tracks_for_solid(SPECS[name], 1 << 20, seed=1)
+    got, refined = run32(gv, SPECS[name], tr)
+    want = oracle.Solid.from_spec(SPECS[name]).query(**tr)
+    compare(got, want, "fp32", name + "-1M")
+
+
+def test_fp32_sampled_16m(gv):
+    """2^24 tracks per solid, in the launch configuration the benchmark times; the
+    oracle checks a seeded sample; codes equal the FP64 pass everywhere."""
+    import torch
+    for name in ("box", "trd", "tube", "cone", "polycone"):
+        spec = SPECS[name]
+        n = 1 << 24
+        tr = W.tracks_for_solid(spec, n, seed=2)
+        s = gv.Solid.from_spec(spec)
+        dev = to_device(tr, torch)
+        ws = gv.Workspace(n)
+        out = gv.query(s, dev, precision="fp32_refine", workspace=ws)
+        out64 = gv.query(s, dev, precision="fp64", want=("inside",))
+        torch.cuda.synchronize()
+        assert torch.equal(out["inside"], out64["inside"]), name
+        g = np.random.default_rng(3)
+        idx = np.sort(g.choice(n, 50000, replace=False))
+        sub = {k: v[idx] for k, v in tr.items()}
+        want = oracle.Solid.from_spec(spec).query(**sub)
+        got = {k: v.cpu().numpy()[idx] for k, v in out.items()}
+        compare(got, want, "fp32", name + "-16M-sample")
+        print(name, "refined fraction", ws.refined() / n)
+        del dev, out, out64
+
+
+def test_fp32_empty_single_and_subsets(gv):
+    import torch
+    s = gv.Solid.from_spec(W.TUBE_M2)
+    ws = gv.Workspace(4096)
+    empty = {k: torch.empty(0, dtype=torch.float64, device="cuda") for k in ("x", "y", "z", "dx", "dy", "dz")}
+    out = gv.query(s, empty, precision="fp32_refine", workspace=ws)
+    torch.cuda.synchronize()
+    assert all(v.numel() == 0 for v in out.values())
+    assert ws.refined() == 0
+    tr = W.tracks_for_solid(W.TUBE_M2, 1, seed=9)
+    got, _ = run32(gv, W.TUBE_M2, tr)
+    compare(got, oracle.Solid.from_spec(W.TUBE_M2).query(**tr), "fp32", "single")
+    spec = SPECS["polycone"]
+    tr = W.tracks_for_solid(spec, 3000, seed=12)
+    want = oracle.Solid.from_spec(spec).query(**tr)
+    dev = to_device(tr, torch)
+    sp = gv.Solid.from_spec(spec)
+    for subset in (("inside",), ("dist_out",), ("safety_in", "safety_out"), ("dist_in", "inside")):
+        out = gv.query(sp, dev, precision="fp32_refine", workspace=ws, want=subset)
+        torch.cuda.synchronize()
+        compare(to_host(out), want, "fp32", f"subset{subset}")
+
+
+def test_fp32_workspace_too_small(gv):
+    import torch
+    s = gv.Solid.from_spec(W.BOX_M1)
+    ws = gv.Workspace(10)
+    tr = to_device(W.box1024(), torch)
+    with pytest.raises(gv.GVError) as e:
+        gv.query(s, tr, precision="fp32_refine", workspace=ws)
+    assert e.value.status == 3
+    with pytest.raises(gv.GVError):
+        gv.query(s, tr, precision="fp32_refine", workspace=None)
+
+
+def test_fp32_edges_tangents_apex(gv):
+    """Degenerate inputs: codes must equal the FP64 pass; where two answers are
+    admissible (a touch of an edge, a tangent ray) the FP32 pass must give the
+    FP64 pass's answer or an admissible one within tolerance."""
+    import torch
+    from tests.test_gpu_parity_fp64 import _edge_tracks
+    cases = [(W.BOX_M1, _edge_tracks())]
+    g = np.random.default_rng(21)
+    n = 4000
+    ph = g.uniform(0, 1.5 * math.pi, n)
+    p = np.stack([20 * np.cos(ph), 20 * np.sin(ph), g.uniform(-29, 29, n)], 1)
+    d = np.stack([-np.sin(ph), np.cos(ph), np.zeros(n)], 1)
+    cases.append((W.TUBE_M2, W.soa(p, d)))
+    z0 = g.uniform(-60, 60, n)
+    p = np.stack([np.zeros(n), np.zeros(n), z0], 1)
+    d = np.stack([np.zeros(n), np.zeros(n), np.where(g.random(n) < 0.5, 1.0, -1.0)], 1)
+    cases.append((W.CONE_M2, W.soa(p, d)))
+    for spec, tr in cases:
+        s = gv.Solid.from_spec(spec)
+        dev = to_device(tr, torch)
+        ws = gv.Workspace(len(tr["x"]))
+        a = to_host(gv.query(s, dev, precision="fp32_refine", workspace=ws))
+        b = to_host(gv.query(s, dev, precision="fp64"))
+        assert (a["inside"] == b["inside"]).all()
+        for k in ("dist_in", "dist_out", "safety_in", "safety_out"):
+            x, y = a[k], b[k]
+            same = (x == y) | (np.isinf(x) & np.isinf(y))
+            fin = np.isfinite(x) & np.isfinite(y) & (x > 0) & (y > 0)
+            tol = np.where(np.abs(y) < 1e-4, 1e-9, 1e-5 * np.abs(y))
+            with np.errstate(invalid="ignore"):
+                same |= fin & (np.abs(x - y) <= tol)
+            assert same.all(), (spec["kind"], k, np.nonzero(~same)[0][:5])
