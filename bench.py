@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=40000, help="tracks per solid for the oracle")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched, navigation and serving forms")
     return ap.parse_args()
 
 
@@ -225,13 +226,8 @@ def run_ours(args):
     ms = t_start.elapsed_time(t_end)
     per_solid_ms = {name: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
                     for i, name in enumerate(names)}
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-
-    queries = world * args.steps * len(names) * n * N_QUERIES
-    value = queries / (ms * 1e-3)
+    ms = reduce_max(ms, world)
+    value = aggregate(args.steps * len(names) * n * N_QUERIES, world, ms)
 
     # dominant kernel: the query pass with the largest mean time per launch
     dom = max(per_solid_ms, key=per_solid_ms.get)
@@ -269,6 +265,14 @@ def run_ours(args):
     }
     if refined is not None:
         line["refined_fraction"] = refined
+    if not args.no_extra:
+        # release the precision-form buffers before the other forms
+        del dev, outs
+        torch.cuda.empty_cache()
+        line["batched"] = bench_batched(gv, torch, max(3, args.steps), peaks)
+        line["nav"] = bench_nav(gv, torch, max(3, args.steps))
+        if rank == 0:
+            line["serving"] = bench_serving(gv, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(inputs, args.cpu_sample)
     if rank == 0:
@@ -305,15 +309,150 @@ def run_e2e(gv, torch, inputs, solids, precision, n, steps, world):
         step()
     b.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(a.elapsed_time(b), world)
     h2d = sum(t.numel() * t.element_size() for tr in host_in.values() for t in tr.values())
     d2h = sum(t.numel() * t.element_size() for tr in host_out.values() for t in tr.values())
-    return {"value": world * steps * len(solids) * n * N_QUERIES / (ms * 1e-3), "unit": "queries/s",
+    return {"value": aggregate(steps * len(solids) * n * N_QUERIES, world, ms), "unit": "queries/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def reduce_max(value: float, world: int, device: str = "cuda") -> float:
+    """Max of a per-rank time over all ranks (the only collective of a replicated run)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
+def _timed(torch, fn, reps):
+    """Mean device time (ms) of fn() over reps calls, CUDA events on the current stream."""
+    stream = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_batched(gv, torch, reps, peaks):
+    """Mixed baskets: 4096 baskets of 16-4096 tracks over 64 solids of the six types,
+    one persistent launch replayed from a CUDA graph, launch shape from the autotuner."""
+    work = W.batched()
+    n = len(work["tracks"]["x"])
+    dev = {k: torch.from_numpy(v).cuda() for k, v in work["tracks"].items()}
+    solids = [gv.Solid.from_spec(sp) for sp in work["solids"]]
+    res = {"workload": "4096 baskets, log-uniform 16-4096 tracks, 64 solids of 6 types", "tracks": n}
+    for prec in ("fp32_refine", "fp64"):
+        b = gv.Batch(solids, work["offset"], work["n"], work["solid"])
+        out = gv.alloc_results(n, "cuda")
+        cfg = b.autotune(dev, out, precision=prec)
+        ms = _timed(torch, lambda: b.run(dev, out, precision=prec), reps)
+        gbs = n * BYTES_PER_TRACK / (ms * 1e-3) / 1e9
+        res[prec] = {"queries_per_s": n * N_QUERIES / (ms * 1e-3), "ms": ms, "config": cfg,
+                     "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
+        if prec == "fp32_refine":
+            res[prec]["refined_fraction"] = b.refined() / n
+    res["fp32_over_fp64"] = res["fp32_refine"]["queries_per_s"] / res["fp64"]["queries_per_s"]
+    return res
+
+
+def bench_nav(gv, torch, reps, n=1 << 22):
+    """Navigation step in the nested detector (world box, 10 tube shells, 32 box cells
+    each): tracks uniform in the world, located once, one step timed."""
+    geo = W.nested_geometry()
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    tr = W.nested_tracks(n, seed=1, geom=geo)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in tr.items()}
+    node = G.locate(dev)
+    torch.cuda.synchronize()
+    # queries per track-step: mother DistanceToOut + SafetyToOut, each daughter DistanceToIn + SafetyIn
+    ndaughters = np.zeros(len(geo["nodes"]) + 1, np.int64)
+    for nd in geo["nodes"][1:]:
+        ndaughters[nd["parent"]] += 1
+    nn = node.cpu().numpy()
+    q_per_step = float(np.mean(2 * (1 + ndaughters[np.where(nn >= 0, nn, len(geo["nodes"]))])))
+    res = {"workload": "nested detector, 2^22 tracks uniform in the world", "queries_per_track_step": q_per_step}
+    ws = gv.Workspace(n)
+    out = None
+    for prec in ("fp32_refine", "fp64"):
+        out = G.step(dev, node, precision=prec, workspace=ws, out=out)
+        ms = _timed(torch, lambda: G.step(dev, node, precision=prec, workspace=ws, out=out), reps)
+        res[prec] = {"steps_per_s": n / (ms * 1e-3), "queries_per_s": n * q_per_step / (ms * 1e-3), "ms": ms}
+        if prec == "fp32_refine":
+            res[prec]["refined_fraction"] = ws.refined() / n
+    res["locate_ms"] = _timed(torch, lambda: G.locate(dev, out=node), max(1, reps // 2))
+    return res
+
+
+def bench_serving(gv, torch, seconds=1.5):
+    """Continuous batching: Poisson arrivals of navigation requests with sizes
+    log-uniform in 1-65536 tracks; saturated throughput first, then p50/p99 latency at
+    50% and 80% of it."""
+    import time as _t
+    geo = W.nested_geometry()
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    srv = gv.Server(G, arena_bytes=2 << 30, max_slots=4096, streams=4, precision="fp32_refine")
+    # 256 requests of log-uniform sizes, packed once into pinned host buffers and
+    # submitted in turn (a buffer may be in flight twice; only timing is read here)
+    sizes = W.request_sizes(256, seed=3)
+    pool = []
+    for k, n in enumerate(sizes):
+        inp, out = gv.Server.buffers(int(n))
+        tr = W.nested_tracks(int(n), seed=900 + k, geom=geo)
+        for c, key in enumerate(("x", "y", "z", "dx", "dy", "dz")):
+            inp[c].copy_(torch.from_numpy(tr[key]))
+        pool.append((inp, out, int(n)))
+
+    def submit(k):
+        inp, out, n = pool[k % len(pool)]
+        return srv.submit(inp, out), n
+
+    # saturated: a burst of requests, all waited
+    burst = 400
+    t0 = _t.perf_counter()
+    tickets = [submit(k) for k in range(burst)]
+    for t, _ in tickets:
+        srv.wait(t, 120)
+    sat_rate = burst / (_t.perf_counter() - t0)
+    res = {"workload": "nested detector, requests log-uniform 1-65536 tracks, Poisson arrivals",
+           "saturated_requests_per_s": sat_rate,
+           "saturated_tracks_per_s": sum(n for _, n in tickets) / (_t.perf_counter() - t0)}
+    g = np.random.default_rng(11)
+    for rho in (0.5, 0.8):
+        srv.reset_stats()
+        rate = rho * sat_rate
+        t_next = _t.perf_counter()
+        live, k = [], burst
+        t_end = t_next + seconds
+        while t_next < t_end:
+            now = _t.perf_counter()
+            if now < t_next:
+                if t_next - now > 2e-4:
+                    _t.sleep((t_next - now) * 0.5)
+                continue
+            live.append(submit(k)[0])
+            k += 1
+            t_next += g.exponential(1.0 / rate)
+        for t in live:
+            srv.wait(t, 120)
+        st = srv.stats()
+        res[f"load_{rho}"] = {"offered_requests_per_s": rate, "completed": st["completed"],
+                              "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                              "launch_groups": st["launches"]}
+    srv.close()
+    return res
 
 
 def gv_supports_fp32(gv) -> bool:

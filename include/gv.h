@@ -129,6 +129,121 @@ gv_status gv_workspace_refined(gv_workspace* ws, void* stream, int64_t* n_refine
 gv_status gv_query(const gv_solid* s, const gv_tracks* tracks, gv_precision prec,
                    const gv_results* res, gv_workspace* ws, void* stream);
 
+/* --- mixed baskets in one launch --------------------------------------------
+ * The scheduler of the paper (Project goals, item 1) collects particles that sit
+ * in the same kind of volume into baskets and hands them to the geometry.  A
+ * batch holds many such baskets, each against its own solid, over one shared
+ * structure-of-arrays track set, and evaluates all of them with one persistent
+ * kernel replayed from a CUDA graph (plus the binary64 worklist pass for
+ * GV_FP32_REFINE). */
+typedef struct {
+  int64_t offset;   /* first track of the basket in the shared arrays */
+  int64_t n;        /* tracks in the basket (>= 0)                    */
+  int32_t solid;    /* index into the batch's solid list              */
+  int32_t reserved; /* must be 0                                       */
+} gv_basket;
+
+/* Launch shape: threads per CTA (128, 256 or 512), tracks per thread in a tile
+ * (1..16; a tile is threads * items tracks of one basket), resident CTAs per SM
+ * (1..32, 0 = as many as fit). */
+typedef struct {
+  int32_t threads, items, ctas_per_sm, reserved;
+} gv_batch_config;
+
+typedef struct gv_batch gv_batch;
+
+/* Copies the solids' descriptors into a device table (the solid handles may be
+ * destroyed afterwards), builds the tile list, and allocates the tile counter
+ * and a worklist as long as the largest offset + n (cudaMalloc). */
+gv_status gv_batch_create(const gv_solid* const* solids, int32_t nsolids, const gv_basket* baskets,
+                          int32_t nbaskets, gv_batch** out);
+gv_status gv_batch_set_config(gv_batch* b, const gv_batch_config* cfg);
+gv_status gv_batch_get_config(const gv_batch* b, gv_batch_config* cfg);
+/* All requested queries for every basket; tracks->n must cover every basket.
+ * The first call with a given set of pointers, precision and configuration
+ * captures a CUDA graph (on a private stream); later calls replay it on
+ * `stream`.  Calls on one batch must not overlap on the GPU. */
+gv_status gv_batch_run(gv_batch* b, const gv_tracks* tracks, gv_precision prec, const gv_results* res,
+                       void* stream);
+/* Times graph replays of every launch shape (128/256/512 threads x 1/2/4 items x
+ * 1..max resident CTAs per SM) on these inputs, keeps the fastest and returns it
+ * in *best (may be NULL).  If the environment variable GV_AUTOTUNE_CACHE names
+ * a file, a stored result for the same workload is reused and new ones are
+ * appended.  Synchronises `stream`. */
+gv_status gv_batch_autotune(gv_batch* b, const gv_tracks* tracks, gv_precision prec, const gv_results* res,
+                            void* stream, gv_batch_config* best);
+/* Tracks of the last GV_FP32_REFINE run sent to binary64 (synchronises `stream`). */
+gv_status gv_batch_refined(gv_batch* b, void* stream, int64_t* n_refined);
+void gv_batch_destroy(gv_batch* b);
+
+/* --- navigation (Physics and Detector geometry subsections: the detector is a
+ *     hierarchy of placed solids; a step ends at the nearest boundary) -------
+ * A geometry is a flat table of placed volumes ("nodes"): node 0 is the world
+ * (parent -1), every other node's parent precedes it, and the daughters of a
+ * node are its children in increasing index.  R (row-major 3x3, nine doubles per
+ * node) and t (three per node) place a node in its parent: p_parent = R p_local
+ * + t.  Host arrays, copied; the solids' descriptors are copied too. */
+typedef struct gv_geom gv_geom;
+gv_status gv_geom_create(int32_t nnodes, const gv_solid* const* node_solid, const int32_t* parent,
+                         const double* R, const double* t, gv_geom** out);
+void gv_geom_destroy(gv_geom* g);
+int32_t gv_geom_node_count(const gv_geom* g);
+/* node[i] = the deepest node containing point i: start at the world and enter
+ * the first daughter (lowest index) that does not classify the point OUTSIDE;
+ * -1 if the point is outside the world.  Binary64 decisions. */
+gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* tracks, int32_t* node, void* stream);
+/* One navigation step for tracks located in node[i] (world coordinates):
+ * step = min(DistanceToOut of the node's solid, DistanceToIn of every daughter in
+ * its own frame), safety = min(SafetyToOut, SafetyToIn of every daughter),
+ * next = the daughter node giving the step or -1 (the track leaves its node);
+ * values of -1 are left out, ties go to the lowest daughter index and a
+ * daughter wins over the mother; no candidate -> step = safety = -1.
+ * GV_FP32_REFINE needs a workspace of >= tracks->n (a binary32 pass; tracks
+ * with an uncertain minimum go to binary64).  Device arrays; async. */
+gv_status gv_nav_step(const gv_geom* g, const gv_tracks* tracks, const int32_t* node, gv_precision prec,
+                      double* step, double* safety, int32_t* next, gv_workspace* ws, void* stream);
+
+/* --- serving: continuous batching of navigation requests (Project goals, item 1:
+ *     the scheduler keeps handing baskets to the geometry) --------------------
+ * A request is n tracks in world coordinates; the service locates them and takes
+ * one navigation step.  A worker thread admits queued requests in arrival order
+ * while a slot is free and the device arena has room, launches everything
+ * admitted together as one group (one H2D copy per request, one launch per
+ * kernel for the group, one D2H copy per request), spreads groups over several
+ * streams so that their copies and kernels overlap, and records each request's
+ * latency from submit to the moment the host sees it complete.  Buffers are host
+ * memory (pinned for speed) that must stay valid until the request is waited:
+ * input 6 n doubles (blocks of n: x, y, z, dx, dy, dz), output 24 n bytes
+ * (blocks of n: step and safety as doubles, next and located node as int32). */
+typedef struct {
+  int64_t arena_bytes; /* device memory for admitted requests (about 192 bytes per track) */
+  int32_t max_slots;   /* requests on the device at once (1..65536)                      */
+  int32_t streams;     /* groups in flight (1..8)                                          */
+  int32_t precision;   /* gv_precision of the navigation step                              */
+  int32_t reserved;    /* 0                                                                */
+} gv_server_config;
+typedef struct {
+  int64_t completed, tracks, launches, queued;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* submit-to-completion latency */
+} gv_server_stats;
+typedef struct gv_server gv_server;
+/* Allocates the arena, per-stream workspaces and streams (cudaMalloc) on the
+ * current device and starts the worker thread.  The geometry must outlive it. */
+gv_status gv_server_create(const gv_geom* g, const gv_server_config* cfg, gv_server** out);
+/* Queues a request and returns its ticket; never blocks.  A request that can
+ * never fit the arena returns GV_ERR_OUT_OF_MEMORY. */
+gv_status gv_server_submit(gv_server* s, int64_t n, const double* host_in, void* host_out, int64_t* ticket);
+/* *done = 1 once the request's results are in host_out. */
+gv_status gv_server_poll(gv_server* s, int64_t ticket, int32_t* done);
+/* Blocks until the request completes (GV_OK, its latency in *latency_ms, may be
+ * NULL, and the ticket is released) or timeout_s passes (GV_ERR_TIMEOUT, the
+ * ticket stays valid).  Every ticket must eventually be waited. */
+gv_status gv_server_wait(gv_server* s, int64_t ticket, double timeout_s, double* latency_ms);
+gv_status gv_server_get_stats(gv_server* s, gv_server_stats* out);
+gv_status gv_server_reset_stats(gv_server* s);
+/* Drains the queue, stops the worker and frees everything. */
+void gv_server_destroy(gv_server* s);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* gv_last_error(void);
 /* Library version string. */

@@ -22,6 +22,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gv_oracle.c")
 _SO = os.path.join(_HERE, "_gv_oracle.so")
+# Test hook: the mutation tests point this at a deliberately broken build.
+_SO_OVERRIDE = os.environ.get("GV_ORACLE_SO")
 _lock = threading.Lock()
 _lib = None
 
@@ -49,8 +51,11 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        build()
-        lib = ctypes.CDLL(_SO)
+        if _SO_OVERRIDE:
+            lib = ctypes.CDLL(_SO_OVERRIDE)
+        else:
+            build()
+            lib = ctypes.CDLL(_SO)
         d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         lib.or_solid_size.restype = i
         for name, args in [

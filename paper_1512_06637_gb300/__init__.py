@@ -139,5 +139,169 @@ def query(solid: Solid, tracks: dict, precision: str = "fp64", out: dict | None 
     return out
 
 
+class Batch:
+    """Many baskets, each against its own solid, over one shared track set (one
+    persistent kernel replayed from a CUDA graph)."""
+
+    def __init__(self, solids: list, offsets, sizes, solid_ids):
+        n = len(offsets)
+        arr = (_abi.Basket * max(n, 1))()
+        for k in range(n):
+            arr[k].offset, arr[k].n, arr[k].solid, arr[k].reserved = int(offsets[k]), int(sizes[k]), int(solid_ids[k]), 0
+        handles = (ctypes.c_void_p * len(solids))(*[s.handle.value for s in solids])
+        h = ctypes.c_void_p()
+        check(lib().gv_batch_create(handles, len(solids), arr, n, ctypes.byref(h)))
+        self.handle = h
+        self.solids = solids  # keep the Python objects alive alongside
+
+    def set_config(self, threads=256, items=2, ctas_per_sm=0):
+        c = _abi.BatchConfig(threads, items, ctas_per_sm, 0)
+        check(lib().gv_batch_set_config(self.handle, ctypes.byref(c)))
+
+    def config(self) -> dict:
+        c = _abi.BatchConfig()
+        check(lib().gv_batch_get_config(self.handle, ctypes.byref(c)))
+        return {"threads": c.threads, "items": c.items, "ctas_per_sm": c.ctas_per_sm}
+
+    def run(self, tracks: dict, out: dict, precision: str = "fp32_refine", stream=None) -> dict:
+        n = tracks["x"].numel()
+        t = tracks_struct(tracks)
+        r = results_struct(out, n)
+        check(lib().gv_batch_run(self.handle, ctypes.byref(t), PRECISIONS[precision], ctypes.byref(r),
+                                 _stream_ptr(stream)))
+        return out
+
+    def autotune(self, tracks: dict, out: dict, precision: str = "fp32_refine", stream=None) -> dict:
+        n = tracks["x"].numel()
+        t = tracks_struct(tracks)
+        r = results_struct(out, n)
+        c = _abi.BatchConfig()
+        check(lib().gv_batch_autotune(self.handle, ctypes.byref(t), PRECISIONS[precision], ctypes.byref(r),
+                                      _stream_ptr(stream), ctypes.byref(c)))
+        return {"threads": c.threads, "items": c.items, "ctas_per_sm": c.ctas_per_sm}
+
+    def refined(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        check(lib().gv_batch_refined(self.handle, _stream_ptr(stream), ctypes.byref(n)))
+        return n.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gv_batch_destroy(h)
+            self.handle = None
+
+
+class Geometry:
+    """A tree of placed volumes (node 0 = world; parents precede children)."""
+
+    def __init__(self, solids: list, nodes: list):
+        import numpy as np
+        self.solids = [s if isinstance(s, Solid) else Solid.from_spec(s) for s in solids]
+        n = len(nodes)
+        hs = (ctypes.c_void_p * n)(*[self.solids[nd["solid"]].handle.value for nd in nodes])
+        par = np.ascontiguousarray([nd["parent"] for nd in nodes], dtype=np.int32)
+        R = np.ascontiguousarray(np.array([np.asarray(nd["R"], float).reshape(9) for nd in nodes]))
+        t = np.ascontiguousarray(np.array([np.asarray(nd["t"], float).reshape(3) for nd in nodes]))
+        h = ctypes.c_void_p()
+        check(lib().gv_geom_create(n, hs, par.ctypes.data_as(ctypes.c_void_p), R.ctypes.data_as(ctypes.c_void_p),
+                                   t.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self.handle = h
+        self.nnodes = n
+
+    def locate(self, tracks: dict, out=None, stream=None):
+        import torch
+        n = tracks["x"].numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=tracks["x"].device)
+        t = tracks_struct(tracks)
+        check(lib().gv_nav_locate(self.handle, ctypes.byref(t), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def step(self, tracks: dict, node, precision: str = "fp64", out: dict | None = None,
+             workspace: Workspace | None = None, stream=None) -> dict:
+        import torch
+        n = tracks["x"].numel()
+        dev = tracks["x"].device
+        if out is None:
+            out = {"step": torch.empty(n, dtype=torch.float64, device=dev),
+                   "safety": torch.empty(n, dtype=torch.float64, device=dev),
+                   "next": torch.empty(n, dtype=torch.int32, device=dev)}
+        t = tracks_struct(tracks)
+        ws = workspace.handle if workspace is not None else None
+        check(lib().gv_nav_step(self.handle, ctypes.byref(t), _ptr(node), PRECISIONS[precision], _ptr(out["step"]),
+                                _ptr(out["safety"]), _ptr(out["next"]), ws, _stream_ptr(stream)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gv_geom_destroy(h)
+            self.handle = None
+
+
+class Server:
+    """Continuous-batching navigation service (locate + one step per track)."""
+
+    def __init__(self, geometry: "Geometry", arena_bytes: int = 1 << 30, max_slots: int = 1024, streams: int = 4,
+                 precision: str = "fp32_refine"):
+        c = _abi.ServerConfig(int(arena_bytes), int(max_slots), int(streams), PRECISIONS[precision], 0)
+        h = ctypes.c_void_p()
+        check(lib().gv_server_create(geometry.handle, ctypes.byref(c), ctypes.byref(h)))
+        self.handle = h
+        self.geometry = geometry
+
+    @staticmethod
+    def buffers(n: int, pin: bool = True):
+        """Host buffers for a request of n tracks: input (6, n) float64, output 24 n bytes."""
+        import torch
+        inp = torch.empty((6, n), dtype=torch.float64)
+        out = torch.empty(24 * max(n, 1), dtype=torch.uint8)
+        if pin:
+            inp, out = inp.pin_memory(), out.pin_memory()
+        return inp, out
+
+    @staticmethod
+    def unpack(out, n: int) -> dict:
+        import numpy as np
+        b = out.numpy()[: 24 * n]
+        return {"step": b[: 8 * n].view(np.float64), "safety": b[8 * n: 16 * n].view(np.float64),
+                "next": b[16 * n: 20 * n].view(np.int32), "node": b[20 * n: 24 * n].view(np.int32)}
+
+    def submit(self, inp, out) -> int:
+        n = inp.shape[1]
+        t = ctypes.c_int64()
+        check(lib().gv_server_submit(self.handle, n, ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int32()
+        check(lib().gv_server_poll(self.handle, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_s: float = 30.0) -> float:
+        lat = ctypes.c_double()
+        check(lib().gv_server_wait(self.handle, ticket, float(timeout_s), ctypes.byref(lat)))
+        return lat.value
+
+    def stats(self) -> dict:
+        st = _abi.ServerStats()
+        check(lib().gv_server_get_stats(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in _abi.ServerStats._fields_}
+
+    def reset_stats(self):
+        check(lib().gv_server_reset_stats(self.handle))
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gv_server_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
 def version() -> str:
     return lib().gv_version().decode()

@@ -23,6 +23,25 @@ _i = ctypes.c_int
 _i64 = ctypes.c_int64
 
 
+class Basket(ctypes.Structure):
+    _fields_ = [("offset", _i64), ("n", _i64), ("solid", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("items", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", _i64), ("max_slots", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", _i64), ("tracks", _i64), ("launches", _i64), ("queued", _i64),
+                ("p50_ms", _d), ("p99_ms", _d), ("mean_ms", _d), ("max_ms", _d)]
+
+
 class Tracks(ctypes.Structure):
     _fields_ = [("x", _p), ("y", _p), ("z", _p), ("dx", _p), ("dy", _p), ("dz", _p), ("n", _i64)]
 
@@ -46,6 +65,26 @@ SIGNATURES = {
     "gv_workspace_destroy": (None, [_p]),
     "gv_workspace_refined": (_i, [_p, _p, _p]),
     "gv_query": (_i, [_p, ctypes.POINTER(Tracks), _i, ctypes.POINTER(Results), _p, _p]),
+    "gv_batch_create": (_i, [_p, ctypes.c_int32, _p, ctypes.c_int32, _p]),
+    "gv_batch_set_config": (_i, [_p, ctypes.POINTER(BatchConfig)]),
+    "gv_batch_get_config": (_i, [_p, ctypes.POINTER(BatchConfig)]),
+    "gv_batch_run": (_i, [_p, ctypes.POINTER(Tracks), _i, ctypes.POINTER(Results), _p]),
+    "gv_batch_autotune": (_i, [_p, ctypes.POINTER(Tracks), _i, ctypes.POINTER(Results), _p,
+                               ctypes.POINTER(BatchConfig)]),
+    "gv_batch_refined": (_i, [_p, _p, _p]),
+    "gv_batch_destroy": (None, [_p]),
+    "gv_geom_create": (_i, [ctypes.c_int32, _p, _p, _p, _p, _p]),
+    "gv_geom_destroy": (None, [_p]),
+    "gv_geom_node_count": (ctypes.c_int32, [_p]),
+    "gv_nav_locate": (_i, [_p, ctypes.POINTER(Tracks), _p, _p]),
+    "gv_nav_step": (_i, [_p, ctypes.POINTER(Tracks), _p, _i, _p, _p, _p, _p, _p]),
+    "gv_server_create": (_i, [_p, ctypes.POINTER(ServerConfig), _p]),
+    "gv_server_submit": (_i, [_p, _i64, _p, _p, _p]),
+    "gv_server_poll": (_i, [_p, _i64, _p]),
+    "gv_server_wait": (_i, [_p, _i64, _d, _p]),
+    "gv_server_get_stats": (_i, [_p, ctypes.POINTER(ServerStats)]),
+    "gv_server_reset_stats": (_i, [_p]),
+    "gv_server_destroy": (None, [_p]),
     "gv_last_error": (ctypes.c_char_p, []),
     "gv_version": (ctypes.c_char_p, []),
 }

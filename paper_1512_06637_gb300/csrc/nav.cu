@@ -1,0 +1,458 @@
+// nav.cu -- the navigation step over a tree of placed volumes.
+//
+// The detector is an ordered hierarchy of placed solids (Detector geometry
+// subsection); in a step the particle moves by the smaller of the physics length
+// and the distance to the next boundary (Physics subsection).  The geometry half
+// of the step, per track located in node v:
+//   step   = min( DistanceToOut of v's solid, DistanceToIn of every daughter c of v
+//                 in c's frame p_c = R_c^T (p - t_c), d_c = R_c^T d ),
+//   safety = min( SafetyToOut of v, SafetyToIn of every daughter ),
+//   next   = the daughter that gives the step, or -1 (the track leaves v);
+// -1 values (a point on the wrong side) are left out; among equal distances the
+// lowest daughter index wins and a daughter wins over the mother.
+// Locate descends from the world into the first daughter (in index order) that
+// does not classify the point as outside.
+//
+// Kernels: binary64, one thread per track; binary32 with kLanes lanes per track
+// (daughters dealt round-robin to the lanes, results combined with warp
+// shuffles), whose tracks with an ambiguous minimum, an uncertain daughter or a
+// polycone are recomputed by the binary64 kernel from a worklist.  World-to-node
+// transforms are composed on the host (binary64, no fused multiply-add) and
+// applied on the device with round-to-nearest operations in a fixed order, so the
+// binary64 results and codes agree with any evaluation that uses the same order.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "gv_internal.h"
+#include "solid_fp32.cuh"
+#include "solid_fp64.cuh"
+
+namespace gv {
+
+struct alignas(16) NodeD {
+  double R[9];      // global rotation (row-major), p_world = R p_local + t
+  double t[3];
+  float Rh[9], Rl[9], th[3], tl[3];  // binary32 splits of R and t
+  int32_t desc;     // index into the solid table
+  int32_t parent;
+  int32_t first;    // daughters: children[first .. first + count)
+  int32_t count;
+};
+
+constexpr int kLanes = 8;  // lanes per track in the binary32 kernel
+
+}  // namespace gv
+
+struct gv_geom {
+  int device;
+  int nnodes, nsolids;
+  gv::NodeD* d_nodes = nullptr;
+  int32_t* d_children = nullptr;
+  gv::Desc* d_solids = nullptr;
+  std::vector<gv::NodeD> nodes;
+  std::vector<int32_t> children;
+  std::vector<gv::Desc> solids;
+};
+
+namespace gv {
+
+using f64::xadd;
+using f64::xmul;
+using f64::xsub;
+
+// binary64 world -> node frame
+__device__ __forceinline__ void to_local64(const NodeD& N, double x, double y, double z, double& lx, double& ly,
+                                           double& lz) {
+  const double v0 = xsub(x, N.t[0]), v1 = xsub(y, N.t[1]), v2 = xsub(z, N.t[2]);
+  lx = xadd(xadd(xmul(N.R[0], v0), xmul(N.R[3], v1)), xmul(N.R[6], v2));
+  ly = xadd(xadd(xmul(N.R[1], v0), xmul(N.R[4], v1)), xmul(N.R[7], v2));
+  lz = xadd(xadd(xmul(N.R[2], v0), xmul(N.R[5], v1)), xmul(N.R[8], v2));
+}
+__device__ __forceinline__ void rot_local64(const NodeD& N, double u, double v, double w, double& lu, double& lv,
+                                            double& lw) {
+  lu = xadd(xadd(xmul(N.R[0], u), xmul(N.R[3], v)), xmul(N.R[6], w));
+  lv = xadd(xadd(xmul(N.R[1], u), xmul(N.R[4], v)), xmul(N.R[7], w));
+  lw = xadd(xadd(xmul(N.R[2], u), xmul(N.R[5], v)), xmul(N.R[8], w));
+}
+
+__device__ __forceinline__ void query64(const Desc& S, const f64::Track& T, unsigned want, f64::Result& R) {
+  if (S.type == kBox) f64::box_query(S, T, want, R);
+  else if (S.type == kTrd || S.type == kTrap) f64::planar_query(S, T, want, R);
+  else f64::pcon_query(S, T, want, R);
+}
+
+__device__ inline int32_t locate64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                   const Desc* __restrict__ solids, double x, double y, double z) {
+  f64::Track T{0, 0, 0, 0, 0, 0};
+  f64::Result R;
+  to_local64(nodes[0], x, y, z, T.x, T.y, T.z);
+  query64(solids[nodes[0].desc], T, f64::kWantCode, R);
+  if (R.code == 2) return -1;
+  int32_t v = 0;
+  for (int depth = 0; depth < 64; depth++) {
+    const NodeD& N = nodes[v];
+    int32_t into = -1;
+    for (int j = 0; j < N.count; j++) {
+      const int32_t c = children[N.first + j];
+      to_local64(nodes[c], x, y, z, T.x, T.y, T.z);
+      query64(solids[nodes[c].desc], T, f64::kWantCode, R);
+      if (R.code != 2) { into = c; break; }
+    }
+    if (into < 0) break;
+    v = into;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(256, 2) k_locate(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                                const Desc* __restrict__ solids, const double* __restrict__ x,
+                                                const double* __restrict__ y, const double* __restrict__ z,
+                                                int32_t* __restrict__ out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = locate64(nodes, children, solids, x[i], y[i], z[i]);
+}
+
+struct NavArgs {
+  const double *x, *y, *z, *u, *v, *w;
+  const int32_t* node;
+  double *step, *safety;
+  int32_t* next;
+  int64_t n;
+};
+
+__device__ inline void nav_step64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                  const Desc* __restrict__ solids, int nnodes, const NavArgs& a, int64_t i) {
+  const int32_t v = a.node[i];
+  if (v < 0 || v >= nnodes) {
+    a.step[i] = -1.0; a.safety[i] = -1.0; a.next[i] = -1;
+    return;
+  }
+  const double x = a.x[i], y = a.y[i], z = a.z[i], u = a.u[i], vv = a.v[i], w = a.w[i];
+  const NodeD& N = nodes[v];
+  f64::Track T;
+  f64::Result R;
+  to_local64(N, x, y, z, T.x, T.y, T.z);
+  rot_local64(N, u, vv, w, T.u, T.v, T.w);
+  query64(solids[N.desc], T, f64::kWantDout | f64::kWantSout, R);
+  double best = R.dout, saf = R.sout;
+  bool have = best >= 0, have_s = saf >= 0;
+  int32_t who = -1;
+  for (int j = 0; j < N.count; j++) {
+    const int32_t c = children[N.first + j];
+    const NodeD& C = nodes[c];
+    to_local64(C, x, y, z, T.x, T.y, T.z);
+    rot_local64(C, u, vv, w, T.u, T.v, T.w);
+    query64(solids[C.desc], T, f64::kWantDin | f64::kWantSin, R);
+    if (R.din >= 0 && (!have || R.din < best || (R.din == best && who == -1))) { best = R.din; who = c; have = true; }
+    if (R.sin >= 0 && (!have_s || R.sin < saf)) { saf = R.sin; have_s = true; }
+  }
+  a.step[i] = have ? best : -1.0;
+  a.safety[i] = have_s ? saf : -1.0;
+  a.next[i] = have ? who : -1;
+}
+
+__global__ void __launch_bounds__(256) k_nav_fp64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                                  const Desc* __restrict__ solids, int nnodes, NavArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    nav_step64(nodes, children, solids, nnodes, a, i);
+}
+
+__global__ void __launch_bounds__(256) k_nav_refine(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                                    const Desc* __restrict__ solids, int nnodes, NavArgs a,
+                                                    const uint32_t* __restrict__ wl,
+                                                    const unsigned long long* __restrict__ cnt) {
+  const int64_t m = (int64_t)*cnt;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+    nav_step64(nodes, children, solids, nnodes, a, wl[j]);
+}
+
+// ------------------------------------------------------------ binary32
+
+// World point (split) -> node frame in double-float; direction rotated in binary32.
+__device__ __forceinline__ f32::TrackF to_local32(const NodeD& N, const f32::TrackF& W) {
+  using f32::F2;
+  using f32::tprod;
+  using f32::tsum;
+  float dh[3], dl[3];
+  const float ph[3] = {W.xh, W.yh, W.zh}, pl[3] = {W.xl, W.yl, W.zl};
+  for (int k = 0; k < 3; k++) {
+    const F2 s = tsum(ph[k], -N.th[k]);
+    const float lo = s.l + (pl[k] - N.tl[k]);
+    dh[k] = s.h + lo;
+    dl[k] = lo - (dh[k] - s.h);
+  }
+  f32::TrackF L;
+  float* oh[3] = {&L.xh, &L.yh, &L.zh};
+  float* ol[3] = {&L.xl, &L.yl, &L.zl};
+  for (int i = 0; i < 3; i++) {
+    const F2 p0 = tprod(N.Rh[i], dh[0]), p1 = tprod(N.Rh[3 + i], dh[1]), p2 = tprod(N.Rh[6 + i], dh[2]);
+    const F2 s1 = tsum(p0.h, p1.h), s2 = tsum(s1.h, p2.h);
+    float lo = (s1.l + s2.l) + ((p0.l + p1.l) + p2.l);
+    lo += N.Rh[i] * dl[0] + N.Rl[i] * dh[0];
+    lo += N.Rh[3 + i] * dl[1] + N.Rl[3 + i] * dh[1];
+    lo += N.Rh[6 + i] * dl[2] + N.Rl[6 + i] * dh[2];
+    const float h = s2.h + lo;
+    *oh[i] = h;
+    *ol[i] = lo - (h - s2.h);
+  }
+  // direction in double-float as well: the quadratic coefficients use its low part
+  const float uh[3] = {W.u, W.v, W.w}, ul[3] = {W.ul, W.vl, W.wl};
+  float* dh_[3] = {&L.u, &L.v, &L.w};
+  float* dl_[3] = {&L.ul, &L.vl, &L.wl};
+  for (int i = 0; i < 3; i++) {
+    const F2 p0 = tprod(N.Rh[i], uh[0]), p1 = tprod(N.Rh[3 + i], uh[1]), p2 = tprod(N.Rh[6 + i], uh[2]);
+    const F2 s1 = tsum(p0.h, p1.h), s2 = tsum(s1.h, p2.h);
+    float lo = (s1.l + s2.l) + ((p0.l + p1.l) + p2.l);
+    lo += N.Rh[i] * ul[0] + N.Rl[i] * uh[0];
+    lo += N.Rh[3 + i] * ul[1] + N.Rl[3 + i] * uh[1];
+    lo += N.Rh[6 + i] * ul[2] + N.Rl[6 + i] * uh[2];
+    const float h = s2.h + lo;
+    *dh_[i] = h;
+    *dl_[i] = lo - (h - s2.h);
+  }
+  L.zkey = 0;
+  L.bad = W.bad;
+  return L;
+}
+
+__device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, unsigned want, f32::R32& R) {
+  R.flag = T.bad;
+  R.code = 1;
+  R.din = R.dout = R.sin = R.sout = 0.f;
+  if (R.flag) return;
+  if (S.type == kBox) f32::box32(S, T, want, R);
+  else if (S.type == kTrd || S.type == kTrap) f32::planar32(S, T, want, R);
+  else if (S.type == kTube) f32::pcon32<true>(S, T, want, R);
+  else if (S.nz == 2) f32::pcon32<false>(S, T, want, R);
+  else R.flag = true;  // polycones with internal planes: binary64 (section choice needs the binary64 z)
+}
+
+// half of the output tolerance: the certified binary32 results are within it
+__device__ __forceinline__ float half_tol(float t) { return 0.5f * (t < 1e-4f ? 1e-9f : 1e-5f * t); }
+
+// Two smallest candidates (value, error, key); key = daughter order, mother = kMother.
+struct Top2 {
+  float b1, e1, b2, e2;
+  int w1;
+  __device__ __forceinline__ void add(float t, float e, int w) {
+    if (t < b1 || (t == b1 && w < w1)) { b2 = b1; e2 = e1; b1 = t; e1 = e; w1 = w; }
+    else if (t < b2) { b2 = t; e2 = e; }
+  }
+};
+
+__global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                                  const Desc* __restrict__ solids, int nnodes, NavArgs a,
+                                                  uint32_t* __restrict__ wl, unsigned long long* __restrict__ cnt) {
+  constexpr int kMother = 0x7ffffffe, kNone = 0x7fffffff;
+  const unsigned lane = threadIdx.x & 31u, sub = lane & (kLanes - 1);
+  const int64_t tracks_per_block = blockDim.x / kLanes;
+  const int64_t stride = (int64_t)gridDim.x * tracks_per_block;
+  const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
+              *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
+              *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
+  for (int64_t base = (int64_t)blockIdx.x * tracks_per_block; base < a.n; base += stride) {
+    const int64_t i = base + threadIdx.x / kLanes;
+    const bool valid = i < a.n;
+    bool flag = false;
+    Top2 top{F_INF, 0.f, F_INF, 0.f, kNone};
+    float saf = F_INF;
+    int32_t v = -1;
+    if (valid) {
+      v = a.node[i];
+      if (v < 0 || v >= nnodes) flag = true;
+    }
+    if (valid && !flag) {
+      const f32::TrackF W = f32::load_track(X, Y, Z, Ux, Uy, Uz, i, true);
+      const NodeD& N = nodes[v];
+      if (sub == 0) {  // the mother on the group's first lane
+        const f32::TrackF L = to_local32(N, W);
+        f32::R32 R;
+        query32(solids[N.desc], L, f32::kWantDout | f32::kWantSout, R);
+        flag |= R.flag || R.dout < 0;  // a point outside its own volume: binary64 decides
+        top.add(R.dout, half_tol(R.dout), kMother);
+        saf = R.sout;
+      }
+      for (int j = sub; j < N.count; j += kLanes) {
+        const NodeD& C = nodes[children[N.first + j]];
+        const f32::TrackF L = to_local32(C, W);
+        f32::R32 R;
+        query32(solids[C.desc], L, f32::kWantDin | f32::kWantSin, R);
+        flag |= R.flag;
+        if (R.din >= 0) top.add(R.din, half_tol(R.din), j);
+        if (R.sin >= 0) saf = fminf(saf, R.sin);
+      }
+    }
+    // combine the group's lanes with shuffles (xor within the group of kLanes)
+    for (int off = kLanes / 2; off > 0; off >>= 1) {
+      const float ob1 = __shfl_xor_sync(0xffffffffu, top.b1, off), oe1 = __shfl_xor_sync(0xffffffffu, top.e1, off);
+      const float ob2 = __shfl_xor_sync(0xffffffffu, top.b2, off), oe2 = __shfl_xor_sync(0xffffffffu, top.e2, off);
+      const int ow1 = __shfl_xor_sync(0xffffffffu, top.w1, off);
+      const float os = __shfl_xor_sync(0xffffffffu, saf, off);
+      const int of = __shfl_xor_sync(0xffffffffu, (int)flag, off);
+      top.add(ob1, oe1, ow1);
+      top.add(ob2, oe2, kNone);
+      saf = fminf(saf, os);
+      flag |= of != 0;
+    }
+    // the winner must be certain: the runner-up's interval may not meet it
+    if (valid && !flag && isfinite(top.b1) && top.b2 - top.e2 <= top.b1 + top.e1) flag = true;
+    if (valid && !flag && !isfinite(top.b1)) flag = true;  // no finite step: binary64 decides
+    if (valid && sub == 0 && !flag) {
+      const NodeD& N = nodes[v];
+      a.step[i] = (double)top.b1;
+      a.safety[i] = isfinite(saf) ? (double)saf : -1.0;
+      a.next[i] = top.w1 == kMother ? -1 : children[N.first + top.w1];
+    }
+    const bool push = valid && sub == 0 && flag;
+    const unsigned m = __ballot_sync(0xffffffffu, push);
+    if (m) {
+      unsigned long long at = 0;
+      const int leader = __ffs(m) - 1;
+      if ((int)lane == leader) at = atomicAdd(cnt, (unsigned long long)__popc(m));
+      at = __shfl_sync(0xffffffffu, at, leader);
+      if (push) wl[at + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+  }
+}
+
+}  // namespace gv
+
+using namespace gv;
+
+static void split_f(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+extern "C" {
+
+gv_status gv_geom_create(int32_t nnodes, const gv_solid* const* node_solid, const int32_t* parent, const double* R,
+                         const double* t, gv_geom** out) {
+  if (!out) return set_error(GV_ERR_INVALID_ARG, "geom: out handle pointer is NULL");
+  if (nnodes <= 0 || !node_solid || !parent || !R || !t) return set_error(GV_ERR_INVALID_ARG, "geom: empty or NULL table");
+  if (parent[0] != -1) return set_error(GV_ERR_INVALID_ARG, "geom: node 0 must be the world (parent -1)");
+  for (int i = 1; i < nnodes; i++)
+    if (parent[i] < 0 || parent[i] >= i) return set_error(GV_ERR_INVALID_ARG, "geom: parents must precede children");
+  for (int i = 0; i < nnodes; i++)
+    if (!node_solid[i]) return set_error(GV_ERR_INVALID_ARG, "geom: NULL solid");
+  for (int i = 0; i < 12 * nnodes; i++)
+    if (!std::isfinite(i < 9 * nnodes ? R[i] : t[i - 9 * nnodes])) return set_error(GV_ERR_INVALID_ARG, "geom: non-finite placement");
+  gv_geom* g = new (std::nothrow) gv_geom;
+  if (!g) return set_error(GV_ERR_OUT_OF_MEMORY, "host allocation failed");
+  g->nnodes = nnodes;
+  g->nodes.resize(nnodes);
+  std::vector<const gv_solid*> uniq;
+  for (int v = 0; v < nnodes; v++) {
+    NodeD& N = g->nodes[v];
+    std::memset(&N, 0, sizeof(N));
+    const double* L = R + 9 * v;
+    const double* tl = t + 3 * v;
+    if (parent[v] < 0) {
+      for (int k = 0; k < 9; k++) N.R[k] = L[k];
+      for (int k = 0; k < 3; k++) N.t[k] = tl[k];
+    } else {  // compose with the parent's global placement (binary64, no fused multiply-add)
+      const NodeD& P = g->nodes[parent[v]];
+      for (int i = 0; i < 3; i++) {
+        for (int j = 0; j < 3; j++)
+          N.R[3 * i + j] = (P.R[3 * i + 0] * L[0 * 3 + j] + P.R[3 * i + 1] * L[1 * 3 + j]) + P.R[3 * i + 2] * L[2 * 3 + j];
+        N.t[i] = ((P.R[3 * i + 0] * tl[0] + P.R[3 * i + 1] * tl[1]) + P.R[3 * i + 2] * tl[2]) + P.t[i];
+      }
+    }
+    for (int k = 0; k < 9; k++) split_f(N.R[k], N.Rh[k], N.Rl[k]);
+    for (int k = 0; k < 3; k++) split_f(N.t[k], N.th[k], N.tl[k]);
+    N.parent = parent[v];
+    int idx = -1;
+    for (size_t k = 0; k < uniq.size(); k++)
+      if (uniq[k] == node_solid[v]) { idx = (int)k; break; }
+    if (idx < 0) { idx = (int)uniq.size(); uniq.push_back(node_solid[v]); }
+    N.desc = idx;
+  }
+  // daughters in increasing node index
+  std::vector<int> cnt(nnodes, 0);
+  for (int v = 1; v < nnodes; v++) cnt[parent[v]]++;
+  int acc = 0;
+  for (int v = 0; v < nnodes; v++) { g->nodes[v].first = acc; g->nodes[v].count = cnt[v]; acc += cnt[v]; }
+  g->children.assign(std::max(acc, 1), 0);
+  std::vector<int> fill(nnodes, 0);
+  for (int v = 1; v < nnodes; v++) {
+    const int p = parent[v];
+    g->children[g->nodes[p].first + fill[p]++] = v;
+  }
+  g->nsolids = (int)uniq.size();
+  for (const gv_solid* s : uniq) g->solids.push_back(s->h);
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_nodes, sizeof(NodeD) * nnodes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_children, sizeof(int32_t) * g->children.size());
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_solids, sizeof(Desc) * g->nsolids);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_nodes, g->nodes.data(), sizeof(NodeD) * nnodes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->d_children, g->children.data(), sizeof(int32_t) * g->children.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_solids, g->solids.data(), sizeof(Desc) * g->nsolids, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    gv_geom_destroy(g);
+    return e == cudaErrorMemoryAllocation ? set_error(GV_ERR_OUT_OF_MEMORY, "geom: cudaMalloc failed") : cuda_error(e, "geom upload");
+  }
+  *out = g;
+  return GV_OK;
+}
+
+void gv_geom_destroy(gv_geom* g) {
+  if (!g) return;
+  if (g->d_nodes) cudaFree(g->d_nodes);
+  if (g->d_children) cudaFree(g->d_children);
+  if (g->d_solids) cudaFree(g->d_solids);
+  delete g;
+}
+
+int32_t gv_geom_node_count(const gv_geom* g) { return g ? g->nnodes : 0; }
+
+gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* t, int32_t* node, void* stream) {
+  if (!g || !t) return set_error(GV_ERR_INVALID_ARG, "locate: NULL geometry or tracks");
+  if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "locate: negative track count");
+  if (t->n == 0) return GV_OK;
+  if (!t->x || !t->y || !t->z || !node) return set_error(GV_ERR_INVALID_ARG, "locate: NULL array");
+  int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sm_count() * 8);
+  k_locate<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, t->x, t->y,
+                                                                 t->z, node, t->n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GV_OK : cuda_error(e, "locate launch");
+}
+
+gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node, gv_precision prec, double* step,
+                      double* safety, int32_t* next, gv_workspace* ws, void* stream) {
+  if (!g || !t) return set_error(GV_ERR_INVALID_ARG, "nav: NULL geometry or tracks");
+  if (prec != GV_FP64 && prec != GV_FP32_REFINE) return set_error(GV_ERR_INVALID_ARG, "unknown precision");
+  if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "nav: negative track count");
+  if (t->n == 0) return GV_OK;
+  if (!t->x || !t->y || !t->z || !t->dx || !t->dy || !t->dz || !node || !step || !safety || !next)
+    return set_error(GV_ERR_INVALID_ARG, "nav: NULL array");
+  const void* ptrs[8] = {t->x, t->y, t->z, t->dx, t->dy, t->dz, step, safety};
+  for (int i = 0; i < 8; i++)
+    if ((uintptr_t)ptrs[i] & 7u) return set_error(GV_ERR_INVALID_ARG, "nav: arrays must be 8-byte aligned");
+  NavArgs a{t->x, t->y, t->z, t->dx, t->dy, t->dz, node, step, safety, next, t->n};
+  cudaStream_t st = (cudaStream_t)stream;
+  const int sms = sm_count();
+  if (prec == GV_FP64) {
+    int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sms * 8);
+    k_nav_fp64<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a);
+  } else {
+    if (!ws) return set_error(GV_ERR_INVALID_ARG, "nav: GV_FP32_REFINE needs a workspace");
+    if (ws->cap < t->n) return set_error(GV_ERR_OUT_OF_MEMORY, "nav: workspace smaller than the basket");
+    cudaError_t e = cudaMemsetAsync(ws->counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_error(e, "nav: counter reset");
+    const int64_t per_block = 256 / kLanes;
+    int64_t blocks = std::min<int64_t>((t->n + per_block - 1) / per_block, (int64_t)sms * 8);
+    k_nav_fp32<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, ws->idx,
+                                                  ws->counter);
+    k_nav_refine<<<(unsigned)(sms * 2), 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, ws->idx,
+                                                       ws->counter);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GV_OK : cuda_error(e, "nav launch");
+}
+
+}  // extern "C"

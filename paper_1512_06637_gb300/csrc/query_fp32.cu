@@ -20,7 +20,7 @@ __device__ __forceinline__ void stage_desc32(Desc& dst, const Desc* __restrict__
 }
 
 template <int FAMILY>
-__global__ void __launch_bounds__(256) k_query_fp32(const Desc* __restrict__ desc, QueryArgs a,
+__global__ void __launch_bounds__(256, FAMILY <= 1 ? 4 : 3) k_query_fp32(const Desc* __restrict__ desc, QueryArgs a,
                                                     uint32_t* __restrict__ worklist,
                                                     unsigned long long* __restrict__ counter) {
   __shared__ Desc S;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_query_fp32(const Desc* __restrict__ des
     const bool valid = i < a.n;
     bool flag = false;
     if (valid) {
-      const f32::TrackF T = f32::load_track(X, Y, Z, Ux, Uy, Uz, i, dirs);
+      const f32::TrackF T = f32::load_track<(FAMILY >= 2)>(X, Y, Z, Ux, Uy, Uz, i, dirs);
       f32::R32 R;
       R.flag = T.bad;
       R.code = 1;

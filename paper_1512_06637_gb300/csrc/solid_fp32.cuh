@@ -37,7 +37,8 @@ enum : unsigned { kWantCode = 1, kWantDin = 2, kWantDout = 4, kWantSin = 8, kWan
 
 struct TrackF {
   float xh, yh, zh, xl, yl, zl;  // point: hi + lo
-  float u, v, w;                 // direction (hi only)
+  float u, v, w;                 // direction: hi
+  float ul, vl, wl;              // direction: lo
   long long zkey;                // order key of z
   bool bad;                      // outside the binary32 range: binary64 only
 };
@@ -51,6 +52,10 @@ struct R32 {
 struct Val {  // value with an absolute error bound
   float v, e;
 };
+
+// "No value" sentinel for interval min/max: finite, so that v - e never forms inf - inf.
+constexpr float BIG = 1e37f;
+__device__ __forceinline__ float unbig(float v) { return v >= BIG ? F_INF : v; }
 
 __device__ __forceinline__ Val vmin(Val a, Val b) {
   const float v = fminf(a.v, b.v);
@@ -66,7 +71,7 @@ __device__ __forceinline__ Val vmax(Val a, Val b) {
 }
 // Certified against the output tolerance (half of it, for margin).
 __device__ __forceinline__ bool certified(Val t) {
-  if (isinf(t.v)) return true;
+  if (isinf(t.v) || t.v >= BIG) return true;
   const float tol = t.v < 1e-4f ? 1e-9f : 1e-5f * t.v;
   return t.e <= 0.5f * tol;
 }
@@ -107,6 +112,7 @@ __device__ __forceinline__ unsigned long long f2d_bits(float f) {
   return ((unsigned long long)hi << 32) | lo;
 }
 
+template <bool DIR_LO = true>
 __device__ __forceinline__ TrackF load_track(const uint2* x, const uint2* y, const uint2* z,
                                              const uint2* u, const uint2* v, const uint2* w,
                                              int64_t i, bool dirs) {
@@ -118,11 +124,22 @@ __device__ __forceinline__ TrackF load_track(const uint2* x, const uint2* y, con
   split(bz, T.zh, T.zl, T.bad);
   T.zkey = order_key((long long)(((unsigned long long)bz.y << 32) | bz.x));
   if (dirs) {
-    T.u = trunc_hi(__ldg(u + i), T.bad);
-    T.v = trunc_hi(__ldg(v + i), T.bad);
-    T.w = trunc_hi(__ldg(w + i), T.bad);
+    const uint2 bu = __ldg(u + i), bv = __ldg(v + i), bw = __ldg(w + i);
+    T.u = trunc_hi(bu, T.bad);
+    T.v = trunc_hi(bv, T.bad);
+    T.w = trunc_hi(bw, T.bad);
+    if (DIR_LO) {
+      bool unused = false;
+      float h;
+      split(bu, h, T.ul, unused);
+      split(bv, h, T.vl, unused);
+      split(bw, h, T.wl, unused);
+    } else {
+      T.ul = T.vl = T.wl = 0.f;
+    }
   } else {
     T.u = T.v = T.w = 0.f;
+    T.ul = T.vl = T.wl = 0.f;
   }
   return T;
 }
@@ -148,6 +165,11 @@ struct SInt {
     lo = fmaxf(lo, g - E);
     hi = fmaxf(hi, g + E);
   }
+  __device__ __forceinline__ void add_int(float g, float glo, float ghi) {
+    s = fmaxf(s, g);
+    lo = fmaxf(lo, glo);
+    hi = fmaxf(hi, ghi);
+  }
   __device__ __forceinline__ float err() const { return fmaxf(s - lo, hi - s); }
 };
 __device__ __forceinline__ SInt sint() { return {-F_INF, -F_INF, -F_INF}; }
@@ -162,10 +184,10 @@ __device__ __forceinline__ int decide(const SInt& S, bool& flag) {
 // Constraint value with its bound.
 struct Gv { float g, E; };
 
-// |p| - D from split values
+// |p| - D from split values (the low part may have either sign: |p| = |ph| + sign(ph) pl)
 __device__ __forceinline__ Gv abs_minus(float ph, float pl, float Dh, float Dl) {
   const float a = fabsf(ph);
-  const float g = (a - Dh) + (fabsf(pl) - Dl);
+  const float g = (a - Dh) + ((ph < 0 ? -pl : pl) - Dl);
   return {g, 4.f * U * fabsf(g) + G42 * (a + Dh) + FLOOR};
 }
 // (n.p - c) with n, c split, p split
@@ -214,29 +236,32 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
       }
     }
   }
+  // 1 / |d_i| once per axis (rounded to within 2 ulp); d_i == 0 gives a huge sentinel
+  float inv[3];
+  for (int i = 0; i < 3; i++) inv[i] = d[i] != 0 ? __frcp_rn(fabsf(d[i])) : 0.f;
   if (want & kWantDout) {
     if (R.code == 2) R.dout = -1.f;
-    else if (R.code == 1 && (any_out || never)) R.dout = 0.f;
+    else if (R.code == 1 && any_out) R.dout = 0.f;
+    else if (R.code == 1) { R.flag = true; R.dout = 0.f; }  // surface, not leaving: binary64
     else {
-      Val acc{F_INF, 0.f};
+      Val acc{BIG, 0.f};
       for (int i = 0; i < 3; i++) {
         if (d[i] == 0) continue;
-        const float ad = fabsf(d[i]);
         float num, en;
         if ((ph[i] < 0) == (d[i] < 0)) { num = -g[i].g; en = g[i].E; }
         else { num = S.Dh[i] + fabsf(ph[i]); en = 4.f * U * num; }
-        const float t = num / ad;
-        acc = vmin(acc, {t, t * (en / num + 4.f * U)});
+        const float t = num * inv[i];
+        acc = vmin(acc, {t, fmaf(en, inv[i], 5.f * U * t)});
       }
       if (!certified(acc)) R.flag = true;
-      R.dout = acc.v;
+      R.dout = unbig(acc.v);
     }
   }
   if (want & kWantDin) {
     if (R.code == 0) R.din = -1.f;
     else if (R.code == 1) R.din = all_in ? 0.f : F_INF;
     else {
-      Val tn{-F_INF, 0.f}, tf{F_INF, 0.f};
+      Val tn{-BIG, 0.f}, tf{BIG, 0.f};
       bool miss = false;
       for (int i = 0; i < 3; i++) {
         if (d[i] == 0) {
@@ -244,10 +269,11 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
           if (g[i].g > 0) miss = true;
           continue;
         }
-        const float ad = fabsf(d[i]);
         const float far = S.Dh[i] + fabsf(ph[i]);
-        const Val acc_near{g[i].g / ad, fabsf(g[i].g / ad) * (g[i].E / fmaxf(fabsf(g[i].g), 1e-30f) + 4.f * U)};
-        const Val plain{far / ad, far / ad * 8.f * U};
+        const float tnear = g[i].g * inv[i];
+        const Val acc_near{tnear, fmaf(g[i].E, inv[i], 5.f * U * fabsf(tnear))};
+        const float tfar = far * inv[i];
+        const Val plain{tfar, 9.f * U * tfar};
         if ((ph[i] < 0) != (d[i] < 0)) {  // toward the face on the point's side
           tn = vmax(tn, acc_near);
           tf = vmin(tf, plain);
@@ -305,35 +331,38 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
       }
     }
   }
+  float igd[4];
+  for (int i = 0; i < 4; i++) igd[i] = __frcp_rn(gd[i]);
+  const float iw = T.w != 0 ? __frcp_rn(fabsf(T.w)) : 0.f;
   if (want & kWantDout) {
     if (R.code == 2) R.dout = -1.f;
-    else if (R.code == 1 && (any_out || never)) R.dout = 0.f;
+    else if (R.code == 1 && any_out) R.dout = 0.f;
+    else if (R.code == 1) { R.flag = true; R.dout = 0.f; }  // surface, not leaving: binary64
     else {
-      Val acc{F_INF, 0.f};
+      Val acc{BIG, 0.f};
       for (int i = 0; i < 4; i++) {
         if (fabsf(gd[i]) <= egd[i]) { R.flag = true; continue; }
         if (gd[i] > 0) {
-          const float t = -g[i].g / gd[i];
-          acc = vmin(acc, {t, fabsf(t) * (g[i].E / fmaxf(fabsf(g[i].g), 1e-30f) + egd[i] / gd[i] + 2.f * U)});
+          const float t = -g[i].g * igd[i];
+          acc = vmin(acc, {t, fmaf(fmaf(fabsf(t), egd[i], g[i].E), igd[i], 5.f * U * fabsf(t))});
         }
       }
       if (T.w != 0) {
-        const float aw = fabsf(T.w);
         float num, en;
         if ((T.zh < 0) == (T.w < 0)) { num = -g[4].g; en = g[4].E; }
         else { num = S.dzh + fabsf(T.zh); en = 4.f * U * num; }
-        const float t = num / aw;
-        acc = vmin(acc, {t, t * (en / num + 4.f * U)});
+        const float t = num * iw;
+        acc = vmin(acc, {t, fmaf(en, iw, 5.f * U * t)});
       }
       if (!certified(acc)) R.flag = true;
-      R.dout = acc.v;
+      R.dout = unbig(acc.v);
     }
   }
   if (want & kWantDin) {
     if (R.code == 0) R.din = -1.f;
     else if (R.code == 1) R.din = all_in ? 0.f : F_INF;
     else {
-      Val tn{-F_INF, 0.f}, tf{F_INF, 0.f};
+      Val tn{-BIG, 0.f}, tf{BIG, 0.f};
       bool miss = false;
       for (int i = 0; i < 4; i++) {
         if (fabsf(gd[i]) <= egd[i]) {
@@ -342,18 +371,18 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
           R.flag = true;
           continue;
         }
-        const float t = -g[i].g / gd[i];
-        const Val tv{t, fabsf(t) * (g[i].E / fmaxf(fabsf(g[i].g), 1e-30f) + egd[i] / fabsf(gd[i]) + 2.f * U)};
+        const float t = -g[i].g * igd[i];
+        const Val tv{t, fmaf(fmaf(fabsf(t), egd[i], g[i].E), fabsf(igd[i]), 5.f * U * fabsf(t))};
         if (gd[i] < 0) tn = vmax(tn, tv); else tf = vmin(tf, tv);
       }
       if (T.w == 0) {
         if (fabsf(g[4].g) <= g[4].E) R.flag = true;
         if (g[4].g > 0) miss = true;
       } else {
-        const float aw = fabsf(T.w);
         const float far = S.dzh + fabsf(T.zh);
-        const Val accn{g[4].g / aw, fabsf(g[4].g / aw) * (g[4].E / fmaxf(fabsf(g[4].g), 1e-30f) + 4.f * U)};
-        const Val plain{far / aw, far / aw * 8.f * U};
+        const float tnear = g[4].g * iw;
+        const Val accn{tnear, fmaf(g[4].E, iw, 5.f * U * fabsf(tnear))};
+        const Val plain{far * iw, far * iw * 9.f * U};
         if ((T.zh < 0) != (T.w < 0)) { tn = vmax(tn, accn); tf = vmin(tf, plain); }
         else { tn = vmax(tn, {-plain.v, plain.e}); tf = vmin(tf, {-accn.v, accn.e}); }
       }
@@ -412,36 +441,59 @@ struct Quad {
   bool hm, hp;
   bool unsure;
 };
+// A0 = u^2 + v^2 in double-float from the split direction
+__device__ __forceinline__ F2 a0_df(const TrackF& T) {
+  const F2 uu = tprod(T.u, T.u), vv = tprod(T.v, T.v);
+  const F2 s = tsum(uu.h, vv.h);
+  const float lo = (s.l + (uu.l + vv.l)) + 2.f * (T.u * T.ul + T.v * T.vl);
+  return {s.h + lo, lo - ((s.h + lo) - s.h)};
+}
+
 template <bool TUBE>
-__device__ inline Quad quad32(float a, float b, const TrackF& T, float radial, float eRadial, float A0,
+__device__ inline Quad quad32(float a, float al, float b, const TrackF& T, float radial, float eRadial, F2 A0,
                               float C, float eC) {
   Quad q;
   q.hm = q.hp = false;
   q.unsure = false;
   q.tm = q.tp = {0.f, 0.f};
   const float P = TUBE ? b : fmaf(a, T.zh, b);
-  const float D = TUBE ? 0.f : a * T.w;
-  const float A = A0 - D * D;
-  const float eA = 6.f * U * (A0 + D * D) + 1e-30f;
+  float D, A, eA;
+  if (TUBE) {
+    D = 0.f;
+    A = A0.h + A0.l;
+    eA = 2.f * U * A + 1e-30f;
+  } else {  // A = A0 - (a w)^2 in double-float: rays nearly along the cone's slope keep their roots
+    const F2 dd = tprod(a, T.w);
+    const float dl = dd.l + (a * T.wl + al * T.w);
+    D = dd.h + dl;
+    const F2 d2 = tprod(dd.h, dd.h);
+    const float d2l = d2.l + 2.f * dd.h * dl;
+    const F2 s = tsum(A0.h, -d2.h);
+    A = s.h + ((s.l + A0.l) - d2l);
+    eA = 4.f * U * fabsf(A) + 2.3e-13f * (A0.h + d2.h) + 1e-30f;
+  }
   const float B = radial - P * D;
   const float eB = eRadial + 6.f * U * fabsf(P * D) + 4.f * U * fabsf(a) * fabsf(T.zh) * fabsf(D);
-  if (A == 0.f && D == 0.f && A0 == 0.f) return q;  // parallel to the axis of a cylinder: no crossing
+  if (A == 0.f && D == 0.f && A0.h == 0.f) return q;  // parallel to the axis of a cylinder: no crossing
   const float disc = B * B - A * C;
   const float eD = 2.f * fabsf(B) * eB + fabsf(A) * eC + fabsf(C) * eA + 4.f * U * (B * B + fabsf(A * C));
   if (disc < -eD) return q;
   if (disc <= eD) { q.unsure = true; return q; }
-  const float sq = sqrtf(disc);
-  const float esq = eD / (2.f * sq) + 2.f * U * sq;
+  const float rs = rsqrtf(disc);
+  const float sq = disc * rs;
+  const float esq = 0.5f * eD * rs + 4.f * U * sq;
   float qq, r1, r2;  // r1 = qq / A, r2 = C / qq
   bool r1_is_plus;
   if (B >= 0) { qq = -(B + sq); r1_is_plus = false; }
   else { qq = sq - B; r1_is_plus = true; }
   const float eq = eB + esq + U * fabsf(qq);
-  r1 = qq / A;
-  r2 = C / qq;
-  const float rel1 = (fabsf(A) <= eA) ? F_INF : eq / fabsf(qq) + eA / fabsf(A) + 2.f * U;
+  const float iA = __frcp_rn(A), iq = __frcp_rn(qq);
+  r1 = qq * iA;
+  r2 = C * iq;
+  const float relq = eq * fabsf(iq);
+  const float rel1 = (fabsf(A) <= eA) ? F_INF : relq + eA * fabsf(iA) + 4.f * U;
   const Val v1{r1, fabsf(r1) * rel1};
-  const Val v2{r2, (eC + fabsf(C) * (eq / fabsf(qq) + 2.f * U)) / fabsf(qq)};
+  const Val v2{r2, fmaf(fabsf(C), relq + 4.f * U, eC) * fabsf(iq)};
   Val vp = r1_is_plus ? v1 : v2, vm = r1_is_plus ? v2 : v1;
   q.tp = vp; q.tm = vm; q.hp = q.hm = true;
   if (!TUBE) {  // keep roots on the nappe a z + b >= 0
@@ -526,19 +578,26 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
   const float gz1 = (T.zh - S.zh[last]) + (T.zl - S.zl[last]);
   const float Ez1 = 4.f * U * fabsf(gz1) + G42 * (fabsf(T.zh) + fabsf(S.zh[last])) + FLOOR;
   Gv pa{-F_INF, 0.f}, pb{-F_INF, 0.f};
-  float gphi = -F_INF, Ephi = 0.f;
+  float gphi = -F_INF, phlo = -F_INF, phhi = -F_INF;  // phi value and the interval holding it
   if (has_phi) {
     pa = phi_plane(S.nsh, S.nsl, T);
     pb = phi_plane(S.neh, S.nel, T);
-    gphi = wide ? fminf(pa.g, pb.g) : fmaxf(pa.g, pb.g);
-    Ephi = fmaxf(pa.E, pb.E);
+    if (wide) {
+      gphi = fminf(pa.g, pb.g);
+      phlo = fminf(pa.g - pa.E, pb.g - pb.E);
+      phhi = fminf(pa.g + pa.E, pb.g + pb.E);
+    } else {
+      gphi = fmaxf(pa.g, pb.g);
+      phlo = fmaxf(pa.g - pa.E, pb.g - pb.E);
+      phhi = fmaxf(pa.g + pa.E, pb.g + pb.E);
+    }
   }
   SInt si = sint();
   si.add(lo_.g, lo_.E);
   if (has_in) si.add(li_.g, li_.E);
   si.add(gz0, Ez0);
   si.add(gz1, Ez1);
-  if (has_phi) si.add(gphi, Ephi);
+  if (has_phi) si.add_int(gphi, phlo, phhi);
   const float s = si.s;
   R.code = decide(si, R.flag);
 
@@ -574,7 +633,7 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
           c.add(S.zh[k] - T.zh, 4.f * U * (fabsf(T.zh) + fabsf(S.zh[k])));
           c.add(T.zh - S.zh[k + 1], 4.f * U * (fabsf(T.zh) + fabsf(S.zh[k + 1])));
         }
-        if (has_phi) c.add(gphi, Ephi);
+        if (has_phi) c.add_int(gphi, phlo, phhi);
         if (R.code == 0 && k == k0) {
           R.sout = -c.s;
           if (!certified({c.s < 0 ? -c.s : c.s, c.err()})) R.flag = true;
@@ -590,9 +649,9 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
   }
   if (!(want & (kWantDin | kWantDout))) return;
 
-  const float radial = T.xh * T.u + T.yh * T.v;
-  const float eRadial = 6.f * U * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;
-  const float A0 = T.u * T.u + T.v * T.v;
+  const float radial = fmaf(T.xh, T.u, fmaf(T.yh, T.v, (T.xh * T.ul + T.xl * T.u) + (T.yh * T.vl + T.yl * T.v)));
+  const float eRadial = 4.f * U * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;
+  const F2 A0 = a0_df(T);
   float nds = 0.f, nde = 0.f, ends = 0.f, ende = 0.f;
   if (has_phi) {
     nds = S.nsh[0] * T.u + S.nsh[1] * T.v;
@@ -679,7 +738,7 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
             C = r2h - P * P;
             eC = 8.f * U * (r2h + P * P) + 1e-30f;
           }
-          const Quad q = quad32<TUBE>(ao, S.obh[k], T, radial, eRadial, A0, C, eC);
+          const Quad q = quad32<TUBE>(ao, TUBE ? 0.f : S.oal[k], S.obh[k], T, radial, eRadial, A0, C, eC);
           if (q.unsure) R.flag = true;
           if (q.hp) {
             if (!apart(q.tp, tlo)) R.flag = true;
@@ -698,7 +757,7 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
             C = r2h - P * P;
             eC = 8.f * U * (r2h + P * P) + 1e-30f;
           }
-          const Quad q = quad32<TUBE>(ai, S.ibh[k], T, radial, eRadial, A0, C, eC);
+          const Quad q = quad32<TUBE>(ai, TUBE ? 0.f : S.ial[k], S.ibh[k], T, radial, eRadial, A0, C, eC);
           if (q.unsure) R.flag = true;
           if (q.hm) {
             if (!apart(q.tm, tlo)) R.flag = true;
@@ -756,7 +815,7 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
             C = r2h - P * P;
             eC = 8.f * U * (r2h + P * P) + 1e-30f;
           }
-          const Quad q = quad32<TUBE>(a, b, T, radial, eRadial, A0, C, eC);
+          const Quad q = quad32<TUBE>(a, TUBE ? 0.f : (side ? S.ial[k] : S.oal[k]), b, T, radial, eRadial, A0, C, eC);
           if (q.unsure) R.flag = true;
           const bool has = side ? q.hp : q.hm;
           const Val tc = side ? q.tp : q.tm;

@@ -12,8 +12,9 @@
 //               DistanceToIn a candidate entry per surface checked against the
 //               other constraints at the entry point.
 // A SURFACE point moving out (some constraint within the band grows along d),
-// or whose ray never gets inside, has DistanceToOut 0; one moving in (every such
-// constraint shrinks) has DistanceToIn 0.  Decision quantities use __dadd_rn/__dmul_rn so that no
+// or whose ray never gets inside (checked halfway to the exit found), has
+// DistanceToOut 0; one moving in (every such constraint shrinks) has
+// DistanceToIn 0.  Decision quantities use __dadd_rn/__dmul_rn so that no
 // multiply-add is fused into them.
 #pragma once
 #include <cuda_runtime.h>
@@ -56,6 +57,30 @@ __device__ __forceinline__ void finish_safety(int code, double s_out_side, doubl
   R.sout = code == 2 ? -1.0 : (code == 1 ? 0.0 : s_in_side);
 }
 
+// Decision quantity s at an arbitrary point (no tolerance applied), per family.
+__device__ inline double box_s(const Desc& S, double x, double y, double z) {
+  return dmax(dmax(xsub(fabs(x), S.D[0]), xsub(fabs(y), S.D[1])), xsub(fabs(z), S.D[2]));
+}
+__device__ inline double planar_s(const Desc& S, double x, double y, double z) {
+  double v = xsub(fabs(z), S.dz);
+  for (int i = 0; i < 4; i++) {
+    const double* P = S.pl[i];
+    v = dmax(v, xsub(xadd(xadd(xmul(P[0], x), xmul(P[1], y)), xmul(P[2], z)), P[3]));
+  }
+  return v;
+}
+__device__ inline double pcon_s(const Desc& S, double x, double y, double z);
+
+// A surface point that is not leaving: the exit t found is meaningful only if the
+// ray is inside (no tolerance) just before it; a ray that never gets inside (a
+// tangent ray from a point a hair outside) leaves at once.  Checked at t / 2.
+template <class SF>
+__device__ __forceinline__ bool inside_before(const Desc& S, const Track& T, double t, SF sf) {
+  if (!(t < GV_INF)) return false;
+  const double h = 0.5 * t;
+  return sf(S, T.x + h * T.u, T.y + h * T.v, T.z + h * T.w) <= 0;
+}
+
 // ------------------------------------------------------------------- box
 
 __device__ inline void box_query(const Desc& S, const Track& T, unsigned want, Result& R) {
@@ -69,15 +94,13 @@ __device__ inline void box_query(const Desc& S, const Track& T, unsigned want, R
   Motion m;
   for (int i = 0; i < 3; i++) m.add(g[i], p[i] < 0 ? -d[i] : d[i]);
   if (want & kWantDout) {
-    // a surface point outside a face (no tolerance) and moving parallel to it never gets inside
-    bool never = false;
-    for (int i = 0; i < 3; i++) never |= (g[i] > 0 && d[i] == 0);
     if (R.code == 2) R.dout = -1.0;
-    else if (R.code == 1 && (m.any_out || never)) R.dout = 0.0;
+    else if (R.code == 1 && m.any_out) R.dout = 0.0;
     else {
       double t = GV_INF;
       for (int i = 0; i < 3; i++)
         if (d[i] != 0) t = dmin(t, (copysign(S.D[i], d[i]) - p[i]) / d[i]);
+      if (R.code == 1 && !inside_before(S, T, t, box_s)) t = 0.0;
       R.dout = t;
     }
   }
@@ -116,15 +139,14 @@ __device__ inline void planar_query(const Desc& S, const Track& T, unsigned want
   Motion m;
   for (int i = 0; i < 5; i++) m.add(g[i], gd[i]);
   if (want & kWantDout) {
-    bool never = false;
-    for (int i = 0; i < 5; i++) never |= (g[i] > 0 && gd[i] == 0);
     if (R.code == 2) R.dout = -1.0;
-    else if (R.code == 1 && (m.any_out || never)) R.dout = 0.0;
+    else if (R.code == 1 && m.any_out) R.dout = 0.0;
     else {
       double t = GV_INF;
       for (int i = 0; i < 4; i++)
         if (gd[i] > 0) t = dmin(t, -g[i] / gd[i]);
       if (T.w != 0) t = dmin(t, (copysign(S.dz, T.w) - T.z) / T.w);
+      if (R.code == 1 && !inside_before(S, T, t, planar_s)) t = 0.0;
       R.dout = t;
     }
   }
@@ -235,6 +257,16 @@ __device__ inline double s_closed(const Desc& S, int k, double r, double z, doub
   return v;
 }
 
+__device__ inline double pcon_s(const Desc& S, double x, double y, double z) {
+  const int last = S.nz - 1;
+  const double r = __dsqrt_rn(xadd(xmul(x, x), xmul(y, y)));
+  const int k = section_of(S, z);
+  double v = dmax(g_out(S.out[k], r, z), dmax(xsub(S.z[0], z), xsub(z, S.z[last])));
+  if (inner_has(S, k)) v = dmax(v, g_in(S.in[k], r, z));
+  if (S.flags & kHasPhi) v = dmax(v, phi_g(S, phi_eval(S, x, y)));
+  return v;
+}
+
 __device__ inline void pcon_query(const Desc& S, const Track& T, unsigned want, Result& R) {
   const int nz = S.nz, last = nz - 1;
   const double r2 = xadd(xmul(T.x, T.x), xmul(T.y, T.y));
@@ -279,26 +311,8 @@ __device__ inline void pcon_query(const Desc& S, const Track& T, unsigned want, 
   const double A0 = xadd(xmul(T.u, T.u), xmul(T.v, T.v));
 
   if (want & kWantDout) {
-    // A surface point that lies outside some constraint (no tolerance) and whose ray
-    // never comes to satisfy it is never inside: it leaves at once.
-    bool never = false;
-    if (R.code == 1 && !m.any_out) {
-      if (go > 0) {
-        const Cross c = line_cross(S.out[k0], T, r2, radial, A0);
-        never |= !(c.hm && c.tm > 0);
-      }
-      if (gi > 0) {
-        const Cross c = line_cross(S.in[k0], T, r2, radial, A0);
-        never |= !(c.hp && c.tp > 0);
-      }
-      never |= (gz0 > 0 && !(T.w > 0)) || (gz1 > 0 && !(T.w < 0));
-      if (has_phi) {
-        if (S.flags & kPhiWide) never |= (gphi > 0 && !(nds < 0) && !(nde < 0));
-        else never |= (f.a > 0 && !(nds < 0)) || (f.b > 0 && !(nde < 0));
-      }
-    }
     if (R.code == 2) R.dout = -1.0;
-    else if (R.code == 1 && (m.any_out || never)) R.dout = 0.0;
+    else if (R.code == 1 && m.any_out) R.dout = 0.0;
     else {
       // phi boundary
       double tphi = GV_INF;
@@ -339,7 +353,9 @@ __device__ inline void pcon_query(const Desc& S, const Track& T, unsigned want, 
         k += T.w > 0 ? 1 : -1;
         tlo = tp;
       }
-      R.dout = dmin(t, tphi);
+      t = dmin(t, tphi);
+      if (R.code == 1 && !inside_before(S, T, t, pcon_s)) t = 0.0;
+      R.dout = t;
     }
   }
 

@@ -1,0 +1,57 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake (a flipped sign, a dropped term, a wrong index, a
+transposed operand, a changed rule) in a copy of the oracle's C source, builds
+it, and runs the pin suite against it; every mutant must make some pin fail.
+The mistakes are planted in the oracle, on the CPU only.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "gv_oracle.c")
+
+MUTANTS = {
+    "box -x plane flipped": ("set_plane(&s->pl[4], -1, 0, 0, dx);", "set_plane(&s->pl[4], 1, 0, 0, dx);"),
+    "tolerance band doubled": ("#define H OR_HALF_TOL", "#define H (2 * OR_HALF_TOL)"),
+    "cone normalisation dropped": ("L->k = 1.0 / sqrt(1.0 + L->a * L->a);", "L->k = 1.0;"),
+    "section index off by one": ("while (k < s->nz - 2 && z >= s->z[k + 1]) k++;",
+                                 "while (k < s->nz - 2 && z >= s->z[k]) k++;"),
+    "phi normal sign": ("s->ns[1] = -cos(sphi);", "s->ns[1] = cos(sphi);"),
+    "phi wide rule inverted": ("s->phi_wide = dphi > pi;", "s->phi_wide = dphi < pi;"),
+    "quadratic root sign": ("const double q = -(B + (B >= 0 ? sq : -sq));",
+                            "const double q = -(B - (B >= 0 ? sq : -sq));"),
+    "gap classified at its start": ("const double mid = j < m ? 0.5 * (lo + t[j]) : 2.0 * lo + 1.0;",
+                                    "const double mid = j < m ? lo : 2.0 * lo + 1.0;"),
+    "polycone safety max instead of min": ("best = dmin(best, s_closed(s, k, p));", "best = dmax(best, s_closed(s, k, p));"),
+    "trap vertex shear sign": ("const double xm = cx - dy * ta, xp = cx + dy * ta;",
+                               "const double xm = cx + dy * ta, xp = cx - dy * ta;"),
+    "rotation not transposed": ("pl[i] = (R[0 * 3 + i] * v[0] + R[1 * 3 + i] * v[1]) + R[2 * 3 + i] * v[2];",
+                                "pl[i] = (R[i * 3 + 0] * v[0] + R[i * 3 + 1] * v[1]) + R[i * 3 + 2] * v[2];"),
+    "daughter tie rule dropped": ("(t == best && who == -1)", "(t == best && who != -1)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site not found: {name}"
+    mutated = src.replace(old, new)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "gv_oracle.c")
+        open(c, "w").write(mutated)
+        with open(os.path.join(ROOT, "oracle", "gv_oracle.h")) as h:
+            open(os.path.join(d, "gv_oracle.h"), "w").write(h.read())
+        so = os.path.join(d, "mutant.so")
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", c,
+                        "-o", so, "-lm"], check=True)
+        env = dict(os.environ, GV_ORACLE_SO=so, GV_ORACLE_THREADS="4")
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode != 0, f"mutant '{name}' survived the pins"

@@ -464,3 +464,23 @@ def test_nav_step_brute_force_tree():
         assert res["step"][i] == pytest.approx(best[0], abs=1e-9)
         assert res["next"][i] == best[1]
         assert res["safety"][i] == pytest.approx(min(saf), abs=1e-9)
+
+
+def test_nav_tie_rules():
+    """Equal distances: a daughter wins over the mother, and the lowest daughter index
+    wins among daughters (world box of half 10; daughters touching its +x face)."""
+    solids = [{"kind": "box", "params": (10.0, 10.0, 10.0)}, {"kind": "box", "params": (10.0, 10.0, 10.0)},
+              {"kind": "box", "params": (2.0, 2.0, 2.0)}]
+    eye = np.eye(3)
+    nodes = [{"solid": 0, "parent": -1, "R": eye, "t": np.zeros(3)},
+             {"solid": 1, "parent": 0, "R": eye, "t": np.array([20.0, 0, 0])},   # entered at x = 10
+             {"solid": 2, "parent": 0, "R": eye, "t": np.array([0.0, 6.0, 0])},  # entered at y = 4
+             {"solid": 2, "parent": 0, "R": eye, "t": np.array([0.0, 6.0, 0])}]  # same as node 2
+    geo = oracle.Geometry(solids, nodes)
+    one, zero = np.ones(1), np.zeros(1)
+    r = geo.nav_step(zero, zero, zero, one, zero, zero, np.zeros(1, np.int32))
+    assert r["step"][0] == 10.0 and r["next"][0] == 1          # daughter beats the mother at 10
+    r = geo.nav_step(zero, zero, zero, zero, one, zero, np.zeros(1, np.int32))
+    assert r["step"][0] == 4.0 and r["next"][0] == 2           # lower index among equal daughters
+    r = geo.nav_step(zero, zero, zero, zero, -one, zero, np.zeros(1, np.int32))
+    assert r["step"][0] == 10.0 and r["next"][0] == -1         # leaves through the mother
