@@ -244,6 +244,24 @@ gv_status gv_server_reset_stats(gv_server* s);
 /* Drains the queue, stops the worker and frees everything. */
 void gv_server_destroy(gv_server* s);
 
+/* The GV_FP32_REFINE query pass without a workspace, for callers that cannot
+ * allocate device memory at call time: a framework that owns all device memory
+ * through its own pool, a serving loop that cannot take cudaMalloc's implicit
+ * device synchronisation, a plug-in with no allocator.  (The paper has no
+ * counterpart; this is an interface convenience of this library.)
+ * Its scratch (refinement worklist and counter) is a fixed device array owned by
+ * the library: every GPU that loads the library holds 4 MiB for it until the
+ * process exits.  At most 1048576 (2^20) tracks per call; larger baskets return
+ * GV_ERR_INVALID_ARG.  The call allocates nothing (no cudaMalloc, no cudaFree).
+ * All calls share the one array: the counter is cleared on `stream` at the start
+ * of each call and the worklist keeps the last call's contents, so calls that
+ * overlap on the GPU race and must be serialised by the caller.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * it before any stream capture.  Results, arguments and errors otherwise as for
+ * gv_query with GV_FP32_REFINE. */
+gv_status gv_query_fp32_static(const gv_solid* s, const gv_tracks* tracks, const gv_results* res,
+                               void* stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* gv_last_error(void);
 /* Library version string. */

@@ -85,6 +85,7 @@ SIGNATURES = {
     "gv_server_get_stats": (_i, [_p, ctypes.POINTER(ServerStats)]),
     "gv_server_reset_stats": (_i, [_p]),
     "gv_server_destroy": (None, [_p]),
+    "gv_query_fp32_static": (_i, [_p, ctypes.POINTER(Tracks), ctypes.POINTER(Results), _p]),
     "gv_last_error": (ctypes.c_char_p, []),
     "gv_version": (ctypes.c_char_p, []),
 }
