@@ -30,7 +30,11 @@ def nvcc() -> str:
 
 
 def flags() -> list[str]:
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # --fmad=false: a multiply-add is fused only where the source writes fmaf/fma, so the
+    # single-solid, batched, navigation and service kernels compute the same bits for a
+    # track (contraction left to the compiler differs between kernels that inline the
+    # same arithmetic).
+    return ARCH + ["-O3", "--fmad=false", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                    "-Xcompiler", "-ffp-contract=off", "-Xptxas", "-warn-spills",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
@@ -49,6 +53,7 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(OBJ, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    headers += [os.path.abspath(__file__), os.path.join(ROOT, "include", "gv.h")]  # flags, ABI
     headers.append(os.path.join(ROOT, "include", "gv.h"))
     srcs = sources()
     objs = [os.path.join(OBJ, os.path.basename(s)[:-3] + ".o") for s in srcs]

@@ -20,7 +20,7 @@ __device__ __forceinline__ void stage_desc32(Desc& dst, const Desc* __restrict__
 }
 
 template <int FAMILY>
-__global__ void __launch_bounds__(256, FAMILY <= 1 ? 4 : 3) k_query_fp32(const Desc* __restrict__ desc, QueryArgs a,
+__global__ void __launch_bounds__(256, FAMILY == 0 ? 4 : (FAMILY == 1 ? 2 : 3)) k_query_fp32(const Desc* __restrict__ desc, QueryArgs a,
                                                     uint32_t* __restrict__ worklist,
                                                     unsigned long long* __restrict__ counter) {
   __shared__ Desc S;
@@ -35,8 +35,24 @@ __global__ void __launch_bounds__(256, FAMILY <= 1 ? 4 : 3) k_query_fp32(const D
               *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
   const unsigned lane = threadIdx.x & 31u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // Polycones of several sections: inside and outside tracks take different paths (one
+  // section and the exit search, against every section and the entry search), so each block first sorts
+  // its chunk of tracks by a binary32 estimate of the side and hands inside tracks to the
+  // first warps and outside tracks to the last; results do not depend on the estimate.
+  __shared__ uint16_t perm[256];
+  __shared__ int n_side[2];
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
-    const int64_t i = base + threadIdx.x;
+    int64_t i = base + threadIdx.x;
+    if (FAMILY == 3 && S.nz > 2) {
+      if (threadIdx.x < 2) n_side[threadIdx.x] = 0;
+      __syncthreads();
+      const bool in_est = i < a.n && f32::inside_estimate(S, X, Y, Z, i);
+      const int at = in_est ? atomicAdd(&n_side[0], 1) : (int)blockDim.x - 1 - atomicAdd(&n_side[1], 1);
+      perm[at] = (uint16_t)threadIdx.x;
+      __syncthreads();
+      i = base + perm[threadIdx.x];
+      __syncthreads();
+    }
     const bool valid = i < a.n;
     bool flag = false;
     if (valid) {

@@ -188,7 +188,7 @@ struct Gv { float g, E; };
 __device__ __forceinline__ Gv abs_minus(float ph, float pl, float Dh, float Dl) {
   const float a = fabsf(ph);
   const float g = (a - Dh) + ((ph < 0 ? -pl : pl) - Dl);
-  return {g, 4.f * U * fabsf(g) + G42 * (a + Dh) + FLOOR};
+  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, a + Dh, FLOOR))};
 }
 // (n.p - c) with n, c split, p split
 __device__ __forceinline__ Gv plane_g(const float* nh, const float* nl, float ch, float cl,
@@ -196,16 +196,22 @@ __device__ __forceinline__ Gv plane_g(const float* nh, const float* nl, float ch
   const F2 p0 = tprod(nh[0], T.xh), p1 = tprod(nh[1], T.yh), p2 = tprod(nh[2], T.zh);
   const F2 s1 = tsum(p0.h, p1.h), s2 = tsum(s1.h, p2.h), s3 = tsum(s2.h, -ch);
   float lo = ((s1.l + s2.l) + s3.l) + ((p0.l + p1.l) + p2.l);
-  lo += nh[0] * T.xl + nl[0] * T.xh;
-  lo += nh[1] * T.yl + nl[1] * T.yh;
-  lo += nh[2] * T.zl + nl[2] * T.zh;
+  lo = fmaf(nh[0], T.xl, fmaf(nl[0], T.xh, lo));
+  lo = fmaf(nh[1], T.yl, fmaf(nl[1], T.yh, lo));
+  lo = fmaf(nh[2], T.zl, fmaf(nl[2], T.zh, lo));
   lo -= cl;
   const float g = s3.h + lo;
-  return {g, 4.f * U * fabsf(g) + G42 * (fabsf(T.xh) + fabsf(T.yh) + fabsf(T.zh) + fabsf(ch)) + FLOOR};
+  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, fabsf(T.xh) + fabsf(T.yh) + fabsf(T.zh) + fabsf(ch), FLOOR))};
 }
 
 // ------------------------------------------------------------------- box
 
+// Both distances from one set of slab times, so that inside and outside tracks run
+// the same instructions: per axis the crossings are a = (|p| - D)/|d| (accurate,
+// the face on the point's side) and b = (D + |p|)/|d| (the far face); moving toward
+// the near face the slab is entered at -b and left at -a, otherwise entered at a
+// and left at b.  DistanceToOut = min exit, DistanceToIn = max entry when it comes
+// before the min exit.
 __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32& R) {
   const float ph[3] = {T.xh, T.yh, T.zh}, pl[3] = {T.xl, T.yl, T.zl}, d[3] = {T.u, T.v, T.w};
   Gv g[3];
@@ -220,74 +226,56 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
   R.sout = R.code == 2 ? -1.f : (R.code == 1 ? 0.f : -s);
   if (R.code != 1 && !certified({fabsf(s), si.err()})) R.flag = true;
   if (!(want & (kWantDin | kWantDout))) return;
-  // surface motion
-  bool any_out = false, all_in = true, never = false;
-  if (R.code == 1) {
-    for (int i = 0; i < 3; i++) {
-      if (fabsf(g[i].g + HF) <= g[i].E) R.flag = true;
-      if (g[i].g >= -HF) {
-        const float gd = ph[i] < 0 ? -d[i] : d[i];
-        if (gd > 0) any_out = true;
-        if (!(gd < 0)) all_in = false;
-      }
-      if (d[i] == 0) {
-        if (fabsf(g[i].g) <= g[i].E) R.flag = true;
-        never |= g[i].g > 0;
-      }
+  Val tn{-BIG, 0.f}, tf{BIG, 0.f};
+  bool miss = false, any_out = false, all_in = true;
+  for (int i = 0; i < 3; i++) {
+    const bool toward = (ph[i] < 0) == (d[i] < 0);  // toward the face on the point's side
+    if (d[i] == 0) {
+      if (fabsf(g[i].g) <= g[i].E) R.flag = true;
+      miss |= g[i].g > 0;
+    } else {
+      const float inv = __frcp_rn(fabsf(d[i]));
+      const float a = g[i].g * inv, b = (S.Dh[i] + fabsf(ph[i])) * inv;
+      const Val A{a, fmaf(g[i].E, inv, 5.f * U * fabsf(a))}, B{b, 9.f * U * b};
+      tn = vmax(tn, toward ? Val{-B.v, B.e} : A);
+      tf = vmin(tf, toward ? Val{-A.v, A.e} : B);
     }
+    // surface start: constraints within the band
+    if (g[i].g >= -HF) {
+      const float gd = ph[i] < 0 ? -d[i] : d[i];
+      any_out |= gd > 0;
+      all_in &= gd < 0;
+    }
+    if (R.code == 1 && fabsf(g[i].g + HF) <= g[i].E) R.flag = true;
   }
-  // 1 / |d_i| once per axis (rounded to within 2 ulp); d_i == 0 gives a huge sentinel
-  float inv[3];
-  for (int i = 0; i < 3; i++) inv[i] = d[i] != 0 ? __frcp_rn(fabsf(d[i])) : 0.f;
   if (want & kWantDout) {
     if (R.code == 2) R.dout = -1.f;
     else if (R.code == 1 && any_out) R.dout = 0.f;
-    else if (R.code == 1) { R.flag = true; R.dout = 0.f; }  // surface, not leaving: binary64
     else {
-      Val acc{BIG, 0.f};
-      for (int i = 0; i < 3; i++) {
-        if (d[i] == 0) continue;
-        float num, en;
-        if ((ph[i] < 0) == (d[i] < 0)) { num = -g[i].g; en = g[i].E; }
-        else { num = S.Dh[i] + fabsf(ph[i]); en = 4.f * U * num; }
-        const float t = num * inv[i];
-        acc = vmin(acc, {t, fmaf(en, inv[i], 5.f * U * t)});
+      if (!certified(tf)) R.flag = true;
+      R.dout = unbig(tf.v);
+      if (R.code == 1) {  // a surface point not leaving: inside (no tolerance) halfway to the exit?
+        const float h = 0.5f * tf.v;
+        float sm = -BIG, em = 0.f;
+        for (int i = 0; i < 3; i++) {
+          const float q = fmaf(h, d[i], ph[i]);
+          sm = fmaxf(sm, fabsf(q) - S.Dh[i]);
+          em = fmaxf(em, 4.f * U * (fabsf(q) + S.Dh[i]) + fabsf(d[i]) * 0.5f * tf.e);
+        }
+        if (!(tf.v < BIG) || fabsf(sm) <= em + 1e-12f) R.flag = true;
+        else if (sm > 0) R.dout = 0.f;
       }
-      if (!certified(acc)) R.flag = true;
-      R.dout = unbig(acc.v);
     }
   }
   if (want & kWantDin) {
     if (R.code == 0) R.din = -1.f;
     else if (R.code == 1) R.din = all_in ? 0.f : F_INF;
+    else if (miss) R.din = F_INF;
     else {
-      Val tn{-BIG, 0.f}, tf{BIG, 0.f};
-      bool miss = false;
-      for (int i = 0; i < 3; i++) {
-        if (d[i] == 0) {
-          if (fabsf(g[i].g) <= g[i].E) R.flag = true;
-          if (g[i].g > 0) miss = true;
-          continue;
-        }
-        const float far = S.Dh[i] + fabsf(ph[i]);
-        const float tnear = g[i].g * inv[i];
-        const Val acc_near{tnear, fmaf(g[i].E, inv[i], 5.f * U * fabsf(tnear))};
-        const float tfar = far * inv[i];
-        const Val plain{tfar, 9.f * U * tfar};
-        if ((ph[i] < 0) != (d[i] < 0)) {  // toward the face on the point's side
-          tn = vmax(tn, acc_near);
-          tf = vmin(tf, plain);
-        } else {
-          tn = vmax(tn, {-plain.v, plain.e});
-          tf = vmin(tf, {-acc_near.v, acc_near.e});
-        }
-      }
-      if (!miss) {
-        if (!apart(tn, tf) || fabsf(tf.v) <= tf.e) R.flag = true;
-        if (tn.v < tf.v && tf.v > 0) {
-          if (!certified(tn)) R.flag = true;
-          R.din = tn.v;
-        } else R.din = F_INF;
+      if (!apart(tn, tf) || fabsf(tf.v) <= tf.e) R.flag = true;
+      if (tn.v < tf.v && tf.v > 0) {
+        if (!certified(tn)) R.flag = true;
+        R.din = tn.v;
       } else R.din = F_INF;
     }
   }
@@ -295,6 +283,9 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
 
 // ------------------------------------------------------------ trd / trap
 
+// One uniform path as for the box: every side plane gives one crossing
+// t = -g / (n.d), an entry when n.d < 0 and an exit when n.d > 0; the z slab
+// gives its two crossings like a box axis.
 __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R32& R) {
   Gv g[5];
   float gd[5], egd[5];
@@ -315,83 +306,73 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
   R.sout = R.code == 2 ? -1.f : (R.code == 1 ? 0.f : -s);
   if (R.code != 1 && !certified({fabsf(s), si.err()})) R.flag = true;
   if (!(want & (kWantDin | kWantDout))) return;
-  bool any_out = false, all_in = true, never = false;
-  if (R.code == 1) {
-    for (int i = 0; i < 5; i++) {
-      if (fabsf(g[i].g + HF) <= g[i].E) R.flag = true;
-      const bool tangent = (i < 4) ? fabsf(gd[i]) <= egd[i] : gd[i] == 0;
-      if (g[i].g >= -HF) {
-        if (tangent && i < 4) R.flag = true;
-        if (gd[i] > 0) any_out = true;
-        if (!(gd[i] < 0)) all_in = false;
-      }
-      if (tangent) {
-        if (fabsf(g[i].g) <= g[i].E || i < 4) { if (g[i].g > -HF) R.flag = true; }
-        never |= g[i].g > 0;
-      }
+  Val tn{-BIG, 0.f}, tf{BIG, 0.f};
+  bool miss = false, any_out = false, all_in = true;
+  for (int i = 0; i < 4; i++) {
+    if (fabsf(gd[i]) <= egd[i]) {  // nearly parallel: which side it stays on must be certain
+      if (fabsf(g[i].g) <= g[i].E || R.code == 1) R.flag = true;
+      miss |= g[i].g > 0;
+      continue;
+    }
+    const float igd = __frcp_rn(gd[i]);
+    const float t = -g[i].g * igd;
+    const Val tv{t, fmaf(fmaf(fabsf(t), egd[i], g[i].E), fabsf(igd), 5.f * U * fabsf(t))};
+    const bool entry = gd[i] < 0;
+    tn = vmax(tn, entry ? tv : Val{-BIG, 0.f});
+    tf = vmin(tf, entry ? Val{BIG, 0.f} : tv);
+  }
+  {  // z slab
+    const bool toward = (T.zh < 0) == (T.w < 0);
+    if (T.w == 0) {
+      if (fabsf(g[4].g) <= g[4].E) R.flag = true;
+      miss |= g[4].g > 0;
+    } else {
+      const float iw = __frcp_rn(fabsf(T.w));
+      const float a = g[4].g * iw, b = (S.dzh + fabsf(T.zh)) * iw;
+      const Val A{a, fmaf(g[4].E, iw, 5.f * U * fabsf(a))}, B{b, 9.f * U * b};
+      tn = vmax(tn, toward ? Val{-B.v, B.e} : A);
+      tf = vmin(tf, toward ? Val{-A.v, A.e} : B);
     }
   }
-  float igd[4];
-  for (int i = 0; i < 4; i++) igd[i] = __frcp_rn(gd[i]);
-  const float iw = T.w != 0 ? __frcp_rn(fabsf(T.w)) : 0.f;
+  for (int i = 0; i < 5; i++) {
+    if (g[i].g >= -HF) {
+      any_out |= gd[i] > 0;
+      all_in &= gd[i] < 0;
+      if (R.code == 1 && i < 4 && fabsf(gd[i]) <= egd[i]) R.flag = true;
+    }
+    if (R.code == 1 && fabsf(g[i].g + HF) <= g[i].E) R.flag = true;
+  }
   if (want & kWantDout) {
     if (R.code == 2) R.dout = -1.f;
     else if (R.code == 1 && any_out) R.dout = 0.f;
-    else if (R.code == 1) { R.flag = true; R.dout = 0.f; }  // surface, not leaving: binary64
     else {
-      Val acc{BIG, 0.f};
-      for (int i = 0; i < 4; i++) {
-        if (fabsf(gd[i]) <= egd[i]) { R.flag = true; continue; }
-        if (gd[i] > 0) {
-          const float t = -g[i].g * igd[i];
-          acc = vmin(acc, {t, fmaf(fmaf(fabsf(t), egd[i], g[i].E), igd[i], 5.f * U * fabsf(t))});
+      if (!certified(tf)) R.flag = true;
+      R.dout = unbig(tf.v);
+      if (R.code == 1) {  // a surface point not leaving: inside (no tolerance) halfway to the exit?
+        const float h = 0.5f * tf.v;
+        const float qx = fmaf(h, T.u, T.xh), qy = fmaf(h, T.v, T.yh), qz = fmaf(h, T.w, T.zh);
+        float sm = fabsf(qz) - S.dzh, em = 4.f * U * (fabsf(qz) + S.dzh);
+        for (int i = 0; i < 4; i++) {
+          const float* P = S.plh[i];
+          const float v = fmaf(P[2], qz, fmaf(P[1], qy, P[0] * qx)) - P[3];
+          sm = fmaxf(sm, v);
+          em = fmaxf(em, 8.f * U * (fabsf(qx) + fabsf(qy) + fabsf(qz) + fabsf(P[3])));
         }
+        em += 0.5f * tf.e + 1e-12f;
+        if (!(tf.v < BIG) || fabsf(sm) <= em) R.flag = true;
+        else if (sm > 0) R.dout = 0.f;
       }
-      if (T.w != 0) {
-        float num, en;
-        if ((T.zh < 0) == (T.w < 0)) { num = -g[4].g; en = g[4].E; }
-        else { num = S.dzh + fabsf(T.zh); en = 4.f * U * num; }
-        const float t = num * iw;
-        acc = vmin(acc, {t, fmaf(en, iw, 5.f * U * t)});
-      }
-      if (!certified(acc)) R.flag = true;
-      R.dout = unbig(acc.v);
     }
   }
   if (want & kWantDin) {
     if (R.code == 0) R.din = -1.f;
     else if (R.code == 1) R.din = all_in ? 0.f : F_INF;
+    else if (miss) R.din = F_INF;
     else {
-      Val tn{-BIG, 0.f}, tf{BIG, 0.f};
-      bool miss = false;
-      for (int i = 0; i < 4; i++) {
-        if (fabsf(gd[i]) <= egd[i]) {
-          // nearly parallel: entering never or much later; only certain if clearly outside
-          if (g[i].g > g[i].E) { miss = true; continue; }
-          R.flag = true;
-          continue;
-        }
-        const float t = -g[i].g * igd[i];
-        const Val tv{t, fmaf(fmaf(fabsf(t), egd[i], g[i].E), fabsf(igd[i]), 5.f * U * fabsf(t))};
-        if (gd[i] < 0) tn = vmax(tn, tv); else tf = vmin(tf, tv);
-      }
-      if (T.w == 0) {
-        if (fabsf(g[4].g) <= g[4].E) R.flag = true;
-        if (g[4].g > 0) miss = true;
-      } else {
-        const float far = S.dzh + fabsf(T.zh);
-        const float tnear = g[4].g * iw;
-        const Val accn{tnear, fmaf(g[4].E, iw, 5.f * U * fabsf(tnear))};
-        const Val plain{far * iw, far * iw * 9.f * U};
-        if ((T.zh < 0) != (T.w < 0)) { tn = vmax(tn, accn); tf = vmin(tf, plain); }
-        else { tn = vmax(tn, {-plain.v, plain.e}); tf = vmin(tf, {-accn.v, accn.e}); }
-      }
-      if (!miss) {
-        if (!apart(tn, tf) || fabsf(tf.v) <= tf.e) R.flag = true;
-        if (tn.v < tf.v && tf.v > 0) {
-          if (!certified(tn)) R.flag = true;
-          R.din = tn.v;
-        } else R.din = F_INF;
+      if (!apart(tn, tf) || fabsf(tf.v) <= tf.e) R.flag = true;
+      if (tn.v < tf.v && tf.v > 0) {
+        if (!certified(tn)) R.flag = true;
+        R.din = tn.v;
       } else R.din = F_INF;
     }
   }
@@ -402,6 +383,9 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
 struct Lat {   // a lateral constraint evaluated in double-float
   float g, E;  // g = (r - R) k  (outer) or (R - r) k (inner)
   float delta, eDelta;  // r - R and its bound
+  float dh, dl;  // r - R in double-float
+  float Rh, Rl;  // R = a z + b at the point, double-float
+  float scale;   // magnitude of the terms of r - R
 };
 
 template <bool TUBE>
@@ -414,14 +398,15 @@ __device__ __forceinline__ Lat lateral(float ah, float al, float bh, float bl, f
     const F2 az = tprod(ah, T.zh);
     const F2 ts = tsum(az.h, bh);
     Rh = ts.h;
-    Rl = ((ts.l + az.l) + (ah * T.zl + al * T.zh)) + bl;
+    Rl = ((ts.l + az.l) + fmaf(ah, T.zl, al * T.zh)) + bl;
     scale = rh + fabsf(az.h) + fabsf(bh);
   }
   const F2 dd = tsum(rh, -Rh);
-  const float delta = dd.h + (dd.l + (rl - Rl));
-  const float eDelta = 4.f * U * fabsf(delta) + G42 * scale + FLOOR;
+  const float dl = dd.l + (rl - Rl);
+  const float delta = dd.h + dl;
+  const float eDelta = fmaf(4.f * U, fabsf(delta), fmaf(G42, scale, FLOOR));
   const float g = outer ? delta * k : -delta * k;
-  return {g, 4.f * U * fabsf(g) + eDelta * k, delta, eDelta};
+  return {g, fmaf(4.f * U, fabsf(g), eDelta * k), delta, eDelta, dd.h, dl, Rh, Rl, scale};
 }
 
 // phi plane value n.p in double-float
@@ -429,13 +414,17 @@ __device__ __forceinline__ Gv phi_plane(const float* nh, const float* nl, const 
   const F2 p0 = tprod(nh[0], T.xh), p1 = tprod(nh[1], T.yh);
   const F2 s1 = tsum(p0.h, p1.h);
   float lo = s1.l + (p0.l + p1.l);
-  lo += nh[0] * T.xl + nl[0] * T.xh;
-  lo += nh[1] * T.yl + nl[1] * T.yh;
+  lo = fmaf(nh[0], T.xl, fmaf(nl[0], T.xh, lo));
+  lo = fmaf(nh[1], T.yl, fmaf(nl[1], T.yh, lo));
   const float g = s1.h + lo;
-  return {g, 4.f * U * fabsf(g) + G42 * (fabsf(T.xh) + fabsf(T.yh)) + FLOOR};
+  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, fabsf(T.xh) + fabsf(T.yh), FLOOR))};
 }
 
-// Crossings of r = a z + b with the track in binary32 with error bounds.
+// Crossings of r = a z + b with the track: f(t) = A t^2 + 2 B t + C = r(t)^2 - R(t)^2,
+// A = u^2 + v^2 - D^2, B = p.d_xy - P D, C = r^2 - P^2 (P = R at the point, D = a w).
+// The discriminant B^2 - A C is formed in double-float from double-float A, B, C: a ray
+// grazing a surface (B^2 close to A C) or nearly along a cone's slope keeps its roots
+// to about 2^-42 of the terms; the roots themselves are then taken in binary32.
 struct Quad {
   Val tm, tp;
   bool hm, hp;
@@ -445,62 +434,88 @@ struct Quad {
 __device__ __forceinline__ F2 a0_df(const TrackF& T) {
   const F2 uu = tprod(T.u, T.u), vv = tprod(T.v, T.v);
   const F2 s = tsum(uu.h, vv.h);
-  const float lo = (s.l + (uu.l + vv.l)) + 2.f * (T.u * T.ul + T.v * T.vl);
+  const float lo = (s.l + (uu.l + vv.l)) + 2.f * fmaf(T.u, T.ul, T.v * T.vl);
   return {s.h + lo, lo - ((s.h + lo) - s.h)};
+}
+// p.d_xy = x u + y v in double-float from the split point and direction
+__device__ __forceinline__ F2 radial_df(const TrackF& T) {
+  const F2 p0 = tprod(T.xh, T.u), p1 = tprod(T.yh, T.v);
+  const F2 s = tsum(p0.h, p1.h);
+  const float lo = (s.l + (p0.l + p1.l)) + fmaf(T.xh, T.ul, fmaf(T.xl, T.u, fmaf(T.yh, T.vl, T.yl * T.v)));
+  return {s.h + lo, lo - ((s.h + lo) - s.h)};
+}
+__device__ __forceinline__ F2 df_norm(float h, float l) {
+  const float s = h + l;
+  return {s, l - (s - h)};
 }
 
 template <bool TUBE>
-__device__ inline Quad quad32(float a, float al, float b, const TrackF& T, float radial, float eRadial, F2 A0,
-                              float C, float eC) {
+__device__ inline Quad quad32(float a, float al, const Lat& L, const TrackF& T, F2 rad, float erad, F2 A0,
+                              float rh, float rl) {
   Quad q;
   q.hm = q.hp = false;
   q.unsure = false;
   q.tm = q.tp = {0.f, 0.f};
-  const float P = TUBE ? b : fmaf(a, T.zh, b);
-  float D, A, eA;
+  // D = a w, P D, B = rad - P D, A = A0 - D^2, C = (r - P)(r + P): all double-float
+  F2 Bd, Ad, D{0.f, 0.f};
+  float eB, eA;
   if (TUBE) {
-    D = 0.f;
-    A = A0.h + A0.l;
-    eA = 2.f * U * A + 1e-30f;
-  } else {  // A = A0 - (a w)^2 in double-float: rays nearly along the cone's slope keep their roots
+    Bd = rad;
+    Ad = A0;
+    eB = erad;
+    eA = G42 * A0.h + 1e-30f;
+  } else {
     const F2 dd = tprod(a, T.w);
-    const float dl = dd.l + (a * T.wl + al * T.w);
-    D = dd.h + dl;
-    const F2 d2 = tprod(dd.h, dd.h);
-    const float d2l = d2.l + 2.f * dd.h * dl;
-    const F2 s = tsum(A0.h, -d2.h);
-    A = s.h + ((s.l + A0.l) - d2l);
-    eA = 4.f * U * fabsf(A) + 2.3e-13f * (A0.h + d2.h) + 1e-30f;
+    D = df_norm(dd.h, dd.l + fmaf(a, T.wl, al * T.w));
+    const F2 pd = tprod(L.Rh, D.h);
+    const float pdl = pd.l + fmaf(L.Rh, D.l, L.Rl * D.h);
+    const F2 bs = tsum(rad.h, -pd.h);
+    Bd = df_norm(bs.h, bs.l + (rad.l - pdl));
+    const F2 d2 = tprod(D.h, D.h);
+    const F2 as = tsum(A0.h, -d2.h);
+    Ad = df_norm(as.h, as.l + (A0.l - fmaf(2.f * D.h, D.l, d2.l)));
+    eB = fmaf(2.f * G42 * fabsf(D.h), L.scale + fabsf(L.Rh), erad);
+    eA = fmaf(G42, A0.h + d2.h, 1e-30f);
   }
-  const float B = radial - P * D;
-  const float eB = eRadial + 6.f * U * fabsf(P * D) + 4.f * U * fabsf(a) * fabsf(T.zh) * fabsf(D);
-  if (A == 0.f && D == 0.f && A0.h == 0.f) return q;  // parallel to the axis of a cylinder: no crossing
-  const float disc = B * B - A * C;
-  const float eD = 2.f * fabsf(B) * eB + fabsf(A) * eC + fabsf(C) * eA + 4.f * U * (B * B + fabsf(A * C));
+  const F2 ps = tsum(rh, L.Rh);
+  const F2 Sd = df_norm(ps.h, ps.l + (rl + L.Rl));  // r + P
+  const F2 cp = tprod(L.dh, Sd.h);
+  const F2 Cd = df_norm(cp.h, cp.l + fmaf(L.dh, Sd.l, L.dl * Sd.h));
+  const float eC = fmaf(fmaf(G42, L.scale, FLOOR), fmaf(2.f, Sd.h, fabsf(L.dh)), 1e-30f);
+  const float A = Ad.h, B = Bd.h, C = Cd.h;
+  if (A == 0.f && D.h == 0.f && A0.h == 0.f) return q;  // parallel to the axis of a cylinder: no crossing
+  const F2 b2 = tprod(Bd.h, Bd.h);
+  const F2 ac = tprod(Ad.h, Cd.h);
+  const F2 ds = tsum(b2.h, -ac.h);
+  const float disc = ds.h + (ds.l + (fmaf(2.f * Bd.h, Bd.l, b2.l) - (ac.l + fmaf(Ad.h, Cd.l, Ad.l * Cd.h))));
+  const float eD = fmaf(2.f * fabsf(B), eB, fmaf(fabsf(A), eC, fmaf(fabsf(C), eA, fmaf(eB, eB,
+                   fmaf(4.f * U * U, b2.h + fabsf(ac.h), fmaf(2.f * U, fabsf(disc), 1e-30f))))));
   if (disc < -eD) return q;
   if (disc <= eD) { q.unsure = true; return q; }
+  const float eB1 = fmaf(U, fabsf(B), eB), eA1 = fmaf(U, fabsf(A), eA), eC1 = fmaf(U, fabsf(C), eC);
   const float rs = rsqrtf(disc);
   const float sq = disc * rs;
-  const float esq = 0.5f * eD * rs + 4.f * U * sq;
-  float qq, r1, r2;  // r1 = qq / A, r2 = C / qq
+  const float esq = fmaf(0.5f * 1.001f * eD, rs, 4.f * U * sq);
+  float qq;  // r1 = qq / A, r2 = C / qq
   bool r1_is_plus;
   if (B >= 0) { qq = -(B + sq); r1_is_plus = false; }
   else { qq = sq - B; r1_is_plus = true; }
-  const float eq = eB + esq + U * fabsf(qq);
+  const float eq = fmaf(U, fabsf(qq), eB1 + esq);
   const float iA = __frcp_rn(A), iq = __frcp_rn(qq);
-  r1 = qq * iA;
-  r2 = C * iq;
+  const float r1 = qq * iA;
+  const float r2 = C * iq;
   const float relq = eq * fabsf(iq);
-  const float rel1 = (fabsf(A) <= eA) ? F_INF : relq + eA * fabsf(iA) + 4.f * U;
+  const float rel1 = (fabsf(A) <= eA1) ? F_INF : fmaf(eA1, fabsf(iA), relq + 4.f * U);
   const Val v1{r1, fabsf(r1) * rel1};
-  const Val v2{r2, fmaf(fabsf(C), relq + 4.f * U, eC) * fabsf(iq)};
-  Val vp = r1_is_plus ? v1 : v2, vm = r1_is_plus ? v2 : v1;
+  const Val v2{r2, fmaf(fabsf(C), relq + 4.f * U, eC1) * fabsf(iq)};
+  const Val vp = r1_is_plus ? v1 : v2, vm = r1_is_plus ? v2 : v1;
   q.tp = vp; q.tm = vm; q.hp = q.hm = true;
   if (!TUBE) {  // keep roots on the nappe a z + b >= 0
+    const float P = L.Rh, Dv = D.h;
     for (int j = 0; j < 2; j++) {
       const Val t = j ? q.tp : q.tm;
-      const float Rt = fmaf(t.v, D, P);
-      const float eR = 4.f * U * (fabsf(P) + fabsf(t.v * D)) + fabsf(D) * t.e + 1e-30f;
+      const float Rt = fmaf(t.v, Dv, P);
+      const float eR = fmaf(4.f * U, fabsf(P) + fabsf(t.v * Dv), fmaf(fabsf(Dv), t.e, fmaf(G42, L.scale, 1e-30f)));
       if (fabsf(Rt) <= eR && isfinite(t.v)) q.unsure = true;
       if (!(Rt >= 0)) { if (j) q.hp = false; else q.hm = false; }
     }
@@ -550,6 +565,90 @@ __device__ __forceinline__ int zrange_in(float lo, float hi, float z0, float zN,
   const float e = q.e + 4.f * U * fabsf(q.z);
   if (fabsf(q.z - lo) <= e || fabsf(q.z - hi) <= e || fabsf(q.z - z0) <= e || fabsf(q.z - zN) <= e) return 0;
   return (q.z >= lo && q.z <= hi && q.z > z0 && q.z < zN) ? 1 : -1;
+}
+
+// ----- interval form of the single-section solids (tube, cone) -----
+// Along the track each constraint holds on an interval (convex regions) whose ends
+// are its crossings; the solid is C minus X1 minus X2 where C is the intersection
+// of the convex constraints (outer surface, z slab, narrow phi) and X1, X2 the
+// excluded convex regions (the hole inside rmin, the wedge cut out by a wide phi).
+struct Iv {
+  Val lo, hi;
+  bool empty;
+};
+__device__ __forceinline__ Iv iv_all() { return {{-BIG, 0.f}, {BIG, 0.f}, false}; }
+__device__ __forceinline__ Iv iv_none() { return {{BIG, 0.f}, {-BIG, 0.f}, true}; }
+// Interval of a convex cone region from its crossings; no crossing: the whole line or
+// nothing, as at the start point (inside if g < 0; |g| within its bound is uncertain).
+__device__ __forceinline__ Iv iv_region(const Quad& q, float g, float Eg, bool& unsure) {
+  if (q.hm || q.hp) return {q.hm ? q.tm : Val{-BIG, 0.f}, q.hp ? q.tp : Val{BIG, 0.f}, false};
+  if (fabsf(g) <= Eg) unsure = true;
+  return g < 0 ? iv_all() : iv_none();
+}
+// Half-space {n.p <= 0} (want_le) or {n.p > 0} crossed at t = -a / nd.
+__device__ __forceinline__ Iv iv_half(float a, float Ea, float nd, float end, bool want_le, bool& unsure) {
+  if (fabsf(nd) <= end) {
+    if (fabsf(a) <= Ea) unsure = true;
+    return ((a <= 0) == want_le) ? iv_all() : iv_none();
+  }
+  const float ind = __frcp_rn(nd);
+  const float t = -a * ind;
+  const Val tv{t, fmaf(fmaf(fabsf(t), end, Ea), fabsf(ind), 5.f * U * fabsf(t))};
+  // moving with nd > 0 the value n.p grows: {n.p <= 0} is before t, {n.p > 0} after
+  const bool before = (nd > 0) == want_le;
+  return before ? Iv{{-BIG, 0.f}, tv, false} : Iv{tv, {BIG, 0.f}, false};
+}
+__device__ __forceinline__ Iv iv_and(const Iv& x, const Iv& y) {
+  if (x.empty || y.empty) return iv_none();
+  return {vmax(x.lo, y.lo), vmin(x.hi, y.hi), false};
+}
+// -1: a < b certainly, +1: a > b certainly, 0: too close to tell
+__device__ __forceinline__ int side(Val a, Val b) { return apart(a, b) ? (a.v < b.v ? -1 : 1) : 0; }
+// a crossing certainly after 0; one that is not is at 0+ or before it
+__device__ __forceinline__ bool after0(Val a) { return a.v > a.e; }
+// side(t, b) and side(b, t) where t may be 0+ (z)
+__device__ __forceinline__ int side_tb(Val t, bool z, Val b) { return z ? (after0(b) ? -1 : 1) : side(t, b); }
+__device__ __forceinline__ int side_bt(Val b, Val t, bool z) { return z ? (after0(b) ? 1 : -1) : side(b, t); }
+// Is the point at t (0+ if z) on the open piece lat \ (X1 u X2)?  +1 certainly, -1
+// certainly not, 0 unsure.
+__device__ __forceinline__ int in_piece(const Iv& lat, const Iv& X1, const Iv& X2, Val t, bool z) {
+  if (lat.empty) return -1;
+  const int a = side_bt(lat.lo, t, z), b = side_tb(t, z, lat.hi);
+  if (a > 0 || b > 0) return -1;
+  int r = (a < 0 && b < 0) ? 1 : 0;
+  const Iv* X[2] = {&X1, &X2};
+  for (int j = 0; j < 2; j++) {
+    if (X[j]->empty) continue;
+    const int c = side_tb(t, z, X[j]->lo), d = side_bt(X[j]->hi, t, z);
+    if (c > 0 && d > 0) return -1;      // certainly inside the excluded part
+    if (!(c < 0 || d < 0)) r = 0;       // not certainly outside it
+  }
+  return r;
+}
+// a <= b certain (false also when too close to tell; the caller flags that)
+__device__ __forceinline__ bool lt_sure(Val a, Val b, bool& unsure) {
+  if (!apart(a, b)) { unsure = true; }
+  return a.v < b.v;
+}
+
+// Binary32 estimate of "inside" for a polycone-family solid from the hi parts only (used
+// to group tracks; no result depends on it).
+__device__ __forceinline__ bool inside_estimate(const Desc& S, const uint2* x, const uint2* y, const uint2* z,
+                                                int64_t i) {
+  bool bad = false;
+  const float px = trunc_hi(__ldg(x + i), bad), py = trunc_hi(__ldg(y + i), bad), pz = trunc_hi(__ldg(z + i), bad);
+  const int nz = S.nz;
+  if (!(pz > S.zh[0] && pz < S.zh[nz - 1])) return false;
+  int k = 0;
+  while (k < nz - 2 && pz >= S.zh[k + 1]) k++;
+  const float r = sqrtf(px * px + py * py);
+  if (r > fmaf(S.oah[k], pz, S.obh[k])) return false;
+  if (((S.inner >> k) & 1u) && r < fmaf(S.iah[k], pz, S.ibh[k])) return false;
+  if (S.flags & kHasPhi) {
+    const float a = S.nsh[0] * px + S.nsh[1] * py, b = S.neh[0] * px + S.neh[1] * py;
+    if (((S.flags & kPhiWide) ? fminf(a, b) : fmaxf(a, b)) > 0.f) return false;
+  }
+  return true;
 }
 
 template <bool TUBE>
@@ -641,6 +740,33 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
         }
         best = vmin(best, {c.s, c.err()});
       }
+      if (R.code == 2 && !certified(best)) {
+        // far sections whose plain bounds may still hold the minimum: redo them in double-float
+        Val best2{BIG, 0.f};
+        for (int k = 0; k < last; k++) {
+          SInt c = sint();
+          const bool near = k >= k0 - 1 && k <= k0 + 1;
+          const float go = (rh - fmaf(S.oah[k], T.zh, S.obh[k])) * S.ok_[k];
+          float v = fmaxf(go, fmaxf(S.zh[k] - T.zh, T.zh - S.zh[k + 1]));
+          if ((S.inner >> k) & 1u) v = fmaxf(v, (fmaf(S.iah[k], T.zh, S.ibh[k]) - rh) * S.ik_[k]);
+          const float ev = 8.f * U * (rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k]) + fabsf(T.zh) + fabsf(S.zh[k]) +
+                                      fabsf(S.zh[k + 1]) + fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k]));
+          if (!near && v - ev > best.v + best.e) continue;  // cannot be the minimum
+          const Lat lo2 = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
+          c.add(lo2.g, lo2.E);
+          if ((S.inner >> k) & 1u) {
+            const Lat li2 = k == k0 ? li_ : lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], rh, rl, T, false);
+            c.add(li2.g, li2.E);
+          }
+          const float gk0 = (S.zh[k] - T.zh) + (S.zl[k] - T.zl);
+          const float gk1 = (T.zh - S.zh[k + 1]) + (T.zl - S.zl[k + 1]);
+          c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + FLOOR);
+          c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + FLOOR);
+          if (has_phi) c.add_int(gphi, phlo, phhi);
+          best2 = vmin(best2, {c.s, c.err()});
+        }
+        best = best2;
+      }
       if (R.code == 2) {
         R.sin = best.v;
         if (!certified(best)) R.flag = true;
@@ -649,8 +775,10 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
   }
   if (!(want & (kWantDin | kWantDout))) return;
 
-  const float radial = fmaf(T.xh, T.u, fmaf(T.yh, T.v, (T.xh * T.ul + T.xl * T.u) + (T.yh * T.vl + T.yl * T.v)));
+  const F2 rad = radial_df(T);
+  const float radial = rad.h;
   const float eRadial = 4.f * U * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;
+  const float erad = G42 * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;  // of rad
   const F2 A0 = a0_df(T);
   float nds = 0.f, nde = 0.f, ends = 0.f, ende = 0.f;
   if (has_phi) {
@@ -687,204 +815,134 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
     }
   }
 
-  if (want & kWantDout) {
-    if (R.code == 2) R.dout = -1.f;
-    else if (R.code == 1 && any_out && !unsure) R.dout = 0.f;
-    else if (R.code == 1) { R.flag = true; R.dout = 0.f; }
-    else {
-      // phi boundary
-      Val tphi{F_INF, 0.f};
-      if (has_phi) {
-        if (!wide) {
-          if (fabsf(nds) <= ends || fabsf(nde) <= ende) R.flag = true;
-          if (nds > 0) { const float t = -pa.g / nds; tphi = vmin(tphi, {t, fabsf(t) * (pa.E / fabsf(pa.g) + ends / nds + 2.f * U)}); }
-          if (nde > 0) { const float t = -pb.g / nde; tphi = vmin(tphi, {t, fabsf(t) * (pb.E / fabsf(pb.g) + ende / nde + 2.f * U)}); }
-        } else {
-          Val tin{-F_INF, 0.f}, tout{F_INF, 0.f};
-          bool never = false;
-          const Gv gg[2] = {pa, pb};
-          const float nd[2] = {nds, nde}, en[2] = {ends, ende};
-          for (int j = 0; j < 2; j++) {
-            if (fabsf(nd[j]) <= en[j]) {
-              if (gg[j].g > gg[j].E) continue;     // already and always beyond this plane
-              if (gg[j].g < -gg[j].E) { never = true; continue; }
-              R.flag = true;
-              continue;
-            }
-            const float t = -gg[j].g / nd[j];
-            const Val tv{t, fabsf(t) * (gg[j].E / fabsf(gg[j].g) + en[j] / fabsf(nd[j]) + 2.f * U)};
-            if (nd[j] > 0) tin = vmax(tin, tv); else tout = vmin(tout, tv);
-          }
-          if (!never) {
-            if (!apart(tin, tout) || fabsf(tin.v) <= tin.e) R.flag = true;
-            if (tin.v < tout.v && tin.v > 0) tphi = tin;
-          }
-        }
-      }
-      // walk the z-sections
-      int k = k0;
-      Val tlo{0.f, 0.f}, t{F_INF, 0.f};
-      for (int guard = 0; guard < kMaxZ; guard++) {
-        Val tl{F_INF, 0.f};
-        {
-          const float ao = TUBE ? 0.f : S.oah[k];
-          float C, eC;
-          if (k == k0) {
-            const float Rp = TUBE ? S.obh[k] : fmaf(ao, T.zh, S.obh[k]);
-            C = lo_.delta * (rh + Rp);
-            eC = lo_.eDelta * (rh + fabsf(Rp)) + 4.f * U * fabsf(C);
-          } else {
-            const float P = TUBE ? S.obh[k] : fmaf(ao, T.zh, S.obh[k]);
-            C = r2h - P * P;
-            eC = 8.f * U * (r2h + P * P) + 1e-30f;
-          }
-          const Quad q = quad32<TUBE>(ao, TUBE ? 0.f : S.oal[k], S.obh[k], T, radial, eRadial, A0, C, eC);
-          if (q.unsure) R.flag = true;
-          if (q.hp) {
-            if (!apart(q.tp, tlo)) R.flag = true;
-            if (q.tp.v > tlo.v) tl = q.tp;
-          }
-        }
-        if ((S.inner >> k) & 1u) {
-          const float ai = TUBE ? 0.f : S.iah[k];
-          float C, eC;
-          if (k == k0) {
-            const float Rp = TUBE ? S.ibh[k] : fmaf(ai, T.zh, S.ibh[k]);
-            C = li_.delta * (rh + Rp);
-            eC = li_.eDelta * (rh + fabsf(Rp)) + 4.f * U * fabsf(C);
-          } else {
-            const float P = TUBE ? S.ibh[k] : fmaf(ai, T.zh, S.ibh[k]);
-            C = r2h - P * P;
-            eC = 8.f * U * (r2h + P * P) + 1e-30f;
-          }
-          const Quad q = quad32<TUBE>(ai, TUBE ? 0.f : S.ial[k], S.ibh[k], T, radial, eRadial, A0, C, eC);
-          if (q.unsure) R.flag = true;
-          if (q.hm) {
-            if (!apart(q.tm, tlo)) R.flag = true;
-            if (q.tm.v > tlo.v) tl = vmin(tl, q.tm);
-          }
-        }
-        Val tp{F_INF, 0.f};
-        bool end;
-        if (T.w > 0) {
-          const float num = (S.zh[k + 1] - T.zh) + (S.zl[k + 1] - T.zl);
-          tp = {num / T.w, fabsf(num / T.w) * 4.f * U + (G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + FLOOR) / T.w};
-          end = (k + 1 == last);
-        } else if (T.w < 0) {
-          const float num = (S.zh[k] - T.zh) + (S.zl[k] - T.zl);
-          tp = {num / T.w, fabsf(num / T.w) * 4.f * U + (G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + FLOOR) / -T.w};
-          end = (k == 0);
-        } else {
-          end = true;
-        }
-        if (isfinite(tl.v) && isfinite(tp.v) && !apart(tl, tp)) R.flag = true;
-        if (tl.v <= tp.v) { t = tl; break; }
-        if (end) { t = tp; break; }
-        k += T.w > 0 ? 1 : -1;
-        tlo = tp;
-      }
-      const Val res = vmin(t, tphi);
-      if (!certified(res)) R.flag = true;
-      R.dout = res.v;
+  // A surface point that is leaving is outside just after 0 (written 0+): DistanceToOut
+  // is 0 and DistanceToIn the first entry after 0+; one that is entering is inside at 0+:
+  // DistanceToIn is 0 and DistanceToOut the end of the stretch holding 0+.  In the
+  // searches below a crossing at 0+ is one not certainly after 0 (it is the surface the
+  // point is on); a result that stays at 0+ contradicts the motion and is flagged.
+  const bool surf = R.code == 1;
+  const bool leaving = surf && any_out && !unsure, entering = surf && all_in && !unsure;
+  if (surf) {
+    if (want & kWantDout) R.dout = 0.f;
+    if (want & kWantDin) R.din = 0.f;
+    if (!leaving && !entering && (want & (kWantDin | kWantDout))) R.flag = true;
+  }
+  if (R.code == 0 && (want & kWantDin)) R.din = -1.f;
+  if (R.code == 2 && (want & kWantDout)) R.dout = -1.f;
+  const bool need_out = (R.code == 0 || entering) && (want & kWantDout);
+  const bool need_in = (R.code == 2 || leaving) && (want & kWantDin);
+  if (!need_out && !need_in) return;
+
+  // Distances in interval form, over the sections the ray meets for t >= 0 in t order.
+  // In section k the ray is inside the solid on C \ (X1 u X2): C = outer region of the
+  // section's line ∩ the section's z slab ∩ narrow phi, X1 = its hole, X2 = the wedge cut
+  // out by a wide phi.  DistanceToIn (outside point) is the first start of such a piece;
+  // DistanceToOut (inside point) follows the stretch that holds the current point, across
+  // internal planes (not surfaces), to its first lateral or end-plane exit.  Inside and
+  // outside tracks run the same loop body.
+  bool u = false;
+  Iv PH = iv_all(), X2 = iv_none();
+  if (has_phi) {
+    if (!wide) PH = iv_and(iv_half(pa.g, pa.E, nds, ends, true, u), iv_half(pb.g, pb.E, nde, ende, true, u));
+    else X2 = iv_and(iv_half(pa.g, pa.E, nds, ends, false, u), iv_half(pb.g, pb.E, nde, ende, false, u));
+    if (!X2.empty && !(X2.lo.v < X2.hi.v)) X2 = iv_none();
+  }
+  const float iw = T.w != 0 ? __frcp_rn(T.w) : 0.f;
+  auto plane_t = [&](int j) -> Val {
+    const float num = (S.zh[j] - T.zh) + (S.zl[j] - T.zl);
+    const float t = num * iw;
+    return {t, fmaf(5.f * U, fabsf(t), fmaf(G42, fabsf(T.zh) + fabsf(S.zh[j]), FLOOR) * fabsf(iw))};
+  };
+  int k, step;
+  bool in_range = true;  // for w == 0: the ray's z inside [z0, zN]
+  if (T.w > 0) { step = 1; k = (T.zkey < S.zkey[0]) ? 0 : k0; }
+  else if (T.w < 0) { step = -1; k = (T.zkey > S.zkey[last]) ? last - 1 : k0; }
+  else {  // the ray stays in the plane z = const: one section or none
+    step = 0; k = k0;
+    in_range = !(gz0 > 0) && !(gz1 > 0);
+    for (int j = k0; j <= k0 + 1; j++) {  // on a plane the pieces on both sides meet: binary64
+      const float gj = (S.zh[j] - T.zh) + (S.zl[j] - T.zl);
+      if (fabsf(gj) <= 4.f * U * fabsf(gj) + G42 * (fabsf(T.zh) + fabsf(S.zh[j])) + FLOOR) u = true;
     }
   }
-
-  if (want & kWantDin) {
-    if (R.code == 0) R.din = -1.f;
-    else if (R.code == 1 && all_in && !unsure) R.din = 0.f;
-    else if (R.code == 1) { R.flag = true; R.din = 0.f; }
-    else {
-      Val best{F_INF, 0.f};
-      const float z0 = S.zh[0], zN = S.zh[last];
-      for (int k = 0; k < last; k++) {
-        if (T.w > 0 && S.zh[k + 1] < T.zh - 1e-3f * fabsf(T.zh)) continue;
-        if (T.w < 0 && S.zh[k] > T.zh + 1e-3f * fabsf(T.zh)) continue;
-        if (T.w == 0 && (T.zh < S.zh[k] - 1e-3f * fabsf(T.zh) - 1e-6f || T.zh > S.zh[k + 1] + 1e-3f * fabsf(T.zh) + 1e-6f)) continue;
-        for (int side = 0; side < 2; side++) {
-          if (side == 1 && !((S.inner >> k) & 1u)) continue;
-          const float a = TUBE ? 0.f : (side ? S.iah[k] : S.oah[k]);
-          const float b = side ? S.ibh[k] : S.obh[k];
-          float C, eC;
-          if (k == k0) {
-            const Lat& L = side ? li_ : lo_;
-            const float Rp = TUBE ? b : fmaf(a, T.zh, b);
-            C = L.delta * (rh + Rp);
-            eC = L.eDelta * (rh + fabsf(Rp)) + 4.f * U * fabsf(C);
-          } else {
-            const float P = TUBE ? b : fmaf(a, T.zh, b);
-            C = r2h - P * P;
-            eC = 8.f * U * (r2h + P * P) + 1e-30f;
-          }
-          const Quad q = quad32<TUBE>(a, TUBE ? 0.f : (side ? S.ial[k] : S.oal[k]), b, T, radial, eRadial, A0, C, eC);
-          if (q.unsure) R.flag = true;
-          const bool has = side ? q.hp : q.hm;
-          const Val tc = side ? q.tp : q.tm;
-          if (!has || !(tc.v > -tc.e) || tc.v - tc.e > best.v + best.e) continue;
-          if (fabsf(tc.v) <= tc.e) { R.flag = true; continue; }
-          const Pt p = advance(T, tc);
-          const int zr = zrange_in(S.zh[k], S.zh[k + 1], z0, zN, p);
-          if (zr == 0) { R.flag = true; continue; }
-          if (zr < 0) continue;
-          const int rr = radial_in(S, k, p, side == 0, side == 1);
-          const int pr = phi_in(S, p);
-          if (rr == 0 || pr == 0) { R.flag = true; continue; }
-          if (rr > 0 && pr > 0) best = vmin(best, tc);
-        }
-      }
-      if (T.w != 0) {
-        const int kk = T.w > 0 ? 0 : last - 1;
-        const int ze = T.w > 0 ? 0 : last;
-        const float num = (S.zh[ze] - T.zh) + (S.zl[ze] - T.zl);
-        const float tv = num / T.w;
-        const Val tc{tv, fabsf(tv) * 4.f * U + (G42 * (fabsf(T.zh) + fabsf(S.zh[ze])) + FLOOR) / fabsf(T.w)};
-        if (tc.v > tc.e && tc.v - tc.e <= best.v + best.e) {
-          Pt p = advance(T, tc);
-          p.z = S.zh[ze];
-          const int rr = radial_in(S, kk, p, false, false);
-          const int pr = phi_in(S, p);
-          if (rr == 0 || pr == 0) R.flag = true;
-          else if (rr > 0 && pr > 0) best = vmin(best, tc);
-        } else if (fabsf(tc.v) <= tc.e) R.flag = true;
-      }
-      if (has_phi) {
-        const Gv gg[2] = {pa, pb};
-        const float nd[2] = {nds, nde}, en[2] = {ends, ende};
-        for (int j = 0; j < 2; j++) {
-          if (fabsf(nd[j]) <= en[j]) { if (fabsf(gg[j].g) <= gg[j].E * 4.f + 1e-6f) R.flag = true; continue; }
-          if (!(nd[j] < 0)) continue;
-          const float tv = -gg[j].g / nd[j];
-          const Val tc{tv, fabsf(tv) * (gg[j].E / fmaxf(fabsf(gg[j].g), 1e-30f) + en[j] / fabsf(nd[j]) + 2.f * U)};
-          if (!(tc.v > -tc.e) || tc.v - tc.e > best.v + best.e) continue;
-          if (fabsf(tc.v) <= tc.e) { R.flag = true; continue; }
-          const Pt p = advance(T, tc);
-          const float ez = p.e + 4.f * U * fabsf(p.z);
-          if (fabsf(p.z - z0) <= ez || fabsf(p.z - zN) <= ez) { R.flag = true; continue; }
-          if (!(p.z > z0 && p.z < zN)) continue;
-          int kq = 0;
-          while (kq < nz - 2 && p.z >= S.zh[kq + 1]) kq++;
-          if (nz > 2) {  // near an internal plane either section may apply
-            const float ek = p.e + 4.f * U * fabsf(p.z);
-            if ((kq + 1 <= nz - 2 && fabsf(p.z - S.zh[kq + 1]) <= ek) || (kq >= 1 && fabsf(p.z - S.zh[kq]) <= ek)) {
-              R.flag = true;
-              continue;
-            }
-          }
-          const int rr = radial_in(S, kq, p, false, false);
-          if (rr == 0) { R.flag = true; continue; }
-          if (rr < 0) continue;
-          if (!wide) {
-            const float* n2 = j == 0 ? S.neh : S.nsh;
-            const float o = n2[0] * p.x + n2[1] * p.y;
-            const float eo = 1.5f * p.e + 4.f * U * (fabsf(p.x) + fabsf(p.y)) + 1e-30f;
-            if (fabsf(o) <= eo) { R.flag = true; continue; }
-            if (o > 0) continue;
-          }
-          best = vmin(best, tc);
-        }
-      }
-      if (!certified(best)) R.flag = true;
-      R.din = best.v;
+  Val tcur{0.f, 0.f};
+  bool out_done = !need_out, in_done = !need_in;
+  Val dout{BIG, 0.f}, din{BIG, 0.f};
+  for (int guard = 0; guard < kMaxZ && !(out_done && in_done); guard++) {
+    Iv slab = iv_all();
+    if (step != 0) {
+      const Val ta = plane_t(k), tb = plane_t(k + 1);
+      slab = step > 0 ? Iv{ta, tb, false} : Iv{tb, ta, false};
+    } else if (!in_range) {
+      slab = iv_none();
     }
+    const bool beyond = !slab.empty && slab.hi.v < -slab.hi.e;  // this section is behind the ray
+    if (!beyond) {
+      const float ao = TUBE ? 0.f : S.oah[k];
+      const Lat Lo = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
+      const Quad qo = quad32<TUBE>(ao, TUBE ? 0.f : S.oal[k], Lo, T, rad, erad, A0, rh, rl);
+      u |= qo.unsure;
+      const Iv lat = iv_and(iv_region(qo, Lo.g, Lo.E, u), PH);  // lateral and phi part of C
+      Iv X1 = iv_none();
+      if ((S.inner >> k) & 1u) {
+        const float ai = TUBE ? 0.f : S.iah[k];
+        const Lat Li = k == k0 ? li_ : lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], rh, rl, T, false);
+        const Quad qi = quad32<TUBE>(ai, TUBE ? 0.f : S.ial[k], Li, T, rad, erad, A0, rh, rl);
+        u |= qi.unsure;
+        X1 = iv_region(qi, -Li.g, Li.E, u);
+        if (!X1.empty && !(X1.lo.v < X1.hi.v)) X1 = iv_none();
+      }
+      const Iv C = iv_and(lat, slab);
+      // first point of C \ (X1 u X2) at t >= 0 (after 0+ for a leaving surface point)
+      if (!in_done && !C.empty && !(leaving && !after0(C.hi))) {
+        bool z = false;  // t is 0+
+        Val t = C.lo;
+        if (leaving ? !after0(C.lo) : !(C.lo.v > 0.f)) { t = Val{0.f, 0.f}; z = leaving; }
+        for (int pass = 0; pass < 2; pass++) {
+          const Iv* X[2] = {&X1, &X2};
+          for (int j = 0; j < 2; j++) {
+            if (X[j]->empty || (!z && t.v == X[j]->hi.v)) continue;
+            const bool after_lo = z ? !after0(X[j]->lo) : !lt_sure(t, X[j]->lo, u);
+            const bool before_hi = z ? after0(X[j]->hi) : lt_sure(t, X[j]->hi, u);
+            if (after_lo && before_hi) { t = X[j]->hi; z = false; }
+          }
+        }
+        if (z || lt_sure(t, C.hi, u)) {
+          if (!(t.v > t.e)) u = true;  // entry strictly after 0 (or 0+)
+          din = t;
+          in_done = true;
+        }
+      }
+      if (!out_done) {
+        // The section must hold tcur on its open piece.
+        const bool z = entering && guard == 0;  // tcur is 0+
+        const int at = in_piece(lat, X1, X2, tcur, z);
+        Val e = lat.hi;  // end of the inside stretch holding tcur
+        if (!X1.empty && (z ? after0(X1.lo) : X1.lo.v > tcur.v)) e = vmin(e, X1.lo);
+        if (!X2.empty && (z ? after0(X2.lo) : X2.lo.v > tcur.v)) e = vmin(e, X2.lo);
+        if (at <= 0) {  // the profile is continuous: the stretch holds tcur unless too close to tell
+          u = true;
+          out_done = true;
+        } else if (step != 0 && lt_sure(slab.hi, e, u)) {  // reaches the far plane first
+          const bool end_plane = (step > 0 && k + 1 == last) || (step < 0 && k == 0);
+          if (end_plane) { dout = slab.hi; out_done = true; }
+          else tcur = slab.hi;
+        } else {
+          dout = e;
+          out_done = true;
+        }
+      }
+    }
+    k += step;
+    if (step == 0 || k < 0 || k > last - 1) break;
+  }
+  if (need_out) {
+    if (!out_done || u || !certified(dout)) R.flag = true;
+    R.dout = unbig(dout.v);
+  }
+  if (need_in) {
+    if (u || !certified(din)) R.flag = true;
+    R.din = in_done ? din.v : F_INF;
   }
 }
 
