@@ -129,6 +129,34 @@ gv_status gv_workspace_refined(gv_workspace* ws, void* stream, int64_t* n_refine
 gv_status gv_query(const gv_solid* s, const gv_tracks* tracks, gv_precision prec,
                    const gv_results* res, gv_workspace* ws, void* stream);
 
+/* --- baskets in host memory ---------------------------------------------------
+ * The same queries for track and result arrays in HOST memory (the exception to
+ * the device-pointer convention above).  A pipeline owns device staging slots
+ * (81 bytes per track of chunk, per slot: the six inputs, the code, four results,
+ * and the refinement worklist) and three CUDA streams of its own; a basket is cut
+ * into chunks and, slot by slot, chunk c+1 is copied in while chunk c is evaluated
+ * and chunk c-1 copied out, so the host link carries both directions at once and
+ * the kernels run under the copies.  Host arrays should be pinned
+ * (cudaHostAlloc/cudaHostRegister); pageable memory gives the same results, with
+ * copies staged by the driver that do not overlap.  The paper's baskets are
+ * filled on the host by the scheduler (Project goals, item 1); this is how they
+ * reach the device. */
+typedef struct gv_pipeline gv_pipeline;
+/* chunk_tracks >= 1 tracks per chunk, 2 <= slots <= 8 staging slots; allocates
+ * slots * chunk_tracks * 85 bytes (cudaMalloc) on the current device. */
+gv_status gv_pipeline_create(int64_t chunk_tracks, int32_t slots, gv_pipeline** out);
+void gv_pipeline_destroy(gv_pipeline* p);
+/* Enqueues gv_query for host arrays (tracks->x..dz and res->* are HOST pointers,
+ * 8-byte aligned, NULL result pointers skip that query).  The work starts after
+ * everything enqueued on `stream` so far, and `stream` waits for its end: the
+ * results are in the host arrays once `stream` has passed this point, and the
+ * host arrays must stay valid and unchanged until then.  Consecutive calls on one
+ * pipeline overlap (the last chunks of one with the first of the next).  A
+ * pipeline must not be used from two threads at once.  Results are bit-identical
+ * to gv_query on the same tracks. */
+gv_status gv_query_host(const gv_solid* s, const gv_tracks* host_tracks, gv_precision prec,
+                        const gv_results* host_results, gv_pipeline* p, void* stream);
+
 /* --- mixed baskets in one launch --------------------------------------------
  * The scheduler of the paper (Project goals, item 1) collects particles that sit
  * in the same kind of volume into baskets and hands them to the geometry.  A

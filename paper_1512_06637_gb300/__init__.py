@@ -139,6 +139,50 @@ def query(solid: Solid, tracks: dict, precision: str = "fp64", out: dict | None 
     return out
 
 
+class Pipeline:
+    """Device staging slots and streams for baskets in host memory (gv_query_host)."""
+
+    def __init__(self, chunk_tracks: int = 1 << 20, slots: int = 3):
+        h = ctypes.c_void_p()
+        check(lib().gv_pipeline_create(int(chunk_tracks), int(slots), ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gv_pipeline_destroy(h)
+            self.handle = None
+
+
+def _host_ptr(a, dtype, n, name):
+    """Address of a contiguous host array (numpy array or CPU torch tensor)."""
+    import numpy as np
+    if a is None:
+        return None
+    if hasattr(a, "is_cuda"):
+        import torch
+        want = torch.int8 if dtype == np.int8 else torch.float64
+        if a.is_cuda or a.dtype != want or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"{name}: expected a contiguous host {want} tensor of {n} elements")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous or a.size != n:
+        raise ValueError(f"{name}: expected a contiguous numpy {np.dtype(dtype)} array of {n} elements")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def query_host(solid: Solid, tracks: dict, out: dict, pipeline: Pipeline, precision: str = "fp64",
+               stream=None) -> dict:
+    """gv_query for host arrays (numpy or CPU tensors, pinned for full speed): enqueued on
+    ``stream``; the results are in ``out`` once that stream has passed this call."""
+    import numpy as np
+    n = int(tracks["x"].size if isinstance(tracks["x"], np.ndarray) else tracks["x"].numel())
+    t = _abi.Tracks(*(_host_ptr(tracks.get(k), np.float64, n, k) for k in ("x", "y", "z", "dx", "dy", "dz")), n)
+    r = _abi.Results(*(_host_ptr(out.get(k), np.int8 if k == "inside" else np.float64, n, k) for k in QUERIES))
+    check(lib().gv_query_host(solid.handle, ctypes.byref(t), PRECISIONS[precision], ctypes.byref(r),
+                              pipeline.handle, _stream_ptr(stream)))
+    return out
+
+
 class Batch:
     """Many baskets, each against its own solid, over one shared track set (one
     persistent kernel replayed from a CUDA graph)."""

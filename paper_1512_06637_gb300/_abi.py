@@ -65,6 +65,9 @@ SIGNATURES = {
     "gv_workspace_destroy": (None, [_p]),
     "gv_workspace_refined": (_i, [_p, _p, _p]),
     "gv_query": (_i, [_p, ctypes.POINTER(Tracks), _i, ctypes.POINTER(Results), _p, _p]),
+    "gv_pipeline_create": (_i, [_i64, ctypes.c_int32, _p]),
+    "gv_pipeline_destroy": (None, [_p]),
+    "gv_query_host": (_i, [_p, ctypes.POINTER(Tracks), _i, ctypes.POINTER(Results), _p, _p]),
     "gv_batch_create": (_i, [_p, ctypes.c_int32, _p, ctypes.c_int32, _p]),
     "gv_batch_set_config": (_i, [_p, ctypes.POINTER(BatchConfig)]),
     "gv_batch_get_config": (_i, [_p, ctypes.POINTER(BatchConfig)]),

@@ -215,6 +215,13 @@ __device__ __forceinline__ f32::TrackF to_local32(const NodeD& N, const f32::Tra
     *dl_[i] = lo - (h - s2.h);
   }
   L.zkey = 0;
+  L.keyed = false;
+  // The local point differs from the binary64 R^T (p - t) by the splits of p and t and the
+  // double-float rounding: 2^-42 of |p|_1 + |t|_1 bounds it per coordinate; the rotated
+  // direction is good to 2^-42 per component.
+  L.fl = fmaf(f32::G42, fabsf(W.xh) + fabsf(W.yh) + fabsf(W.zh) + fabsf(N.th[0]) + fabsf(N.th[1]) + fabsf(N.th[2]),
+              f32::FLOOR);
+  L.dfl = f32::G42;
   L.bad = W.bad;
   return L;
 }
@@ -224,11 +231,11 @@ __device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, uns
   R.code = 1;
   R.din = R.dout = R.sin = R.sout = 0.f;
   if (R.flag) return;
-  if (S.type == kBox) f32::box32(S, T, want, R);
-  else if (S.type == kTrd || S.type == kTrap) f32::planar32(S, T, want, R);
-  else if (S.type == kTube) f32::pcon32<true>(S, T, want, R);
-  else if (S.nz == 2) f32::pcon32<false>(S, T, want, R);
-  else R.flag = true;  // polycones with internal planes: binary64 (section choice needs the binary64 z)
+  // frame tracks: the bounds add the local coordinates' and direction's own errors
+  if (S.type == kBox) f32::box32<true>(S, T, want, R);
+  else if (S.type == kTrd || S.type == kTrap) f32::planar32<true>(S, T, want, R);
+  else if (S.type == kTube) f32::pcon32<true, true>(S, T, want, R);
+  else f32::pcon32<false, true>(S, T, want, R);
 }
 
 // half of the output tolerance: the certified binary32 results are within it

@@ -39,7 +39,10 @@ struct TrackF {
   float xh, yh, zh, xl, yl, zl;  // point: hi + lo
   float u, v, w;                 // direction: hi
   float ul, vl, wl;              // direction: lo
-  long long zkey;                // order key of z
+  long long zkey;                // order key of z (query kernels; keyed = true)
+  float fl;                      // absolute error of each point coordinate beyond 2^-46 |x|
+  float dfl;                     // absolute error of each direction component (frame tracks)
+  bool keyed;                    // zkey holds the binary64 z (false after a frame change)
   bool bad;                      // outside the binary32 range: binary64 only
 };
 
@@ -118,6 +121,9 @@ __device__ __forceinline__ TrackF load_track(const uint2* x, const uint2* y, con
                                              int64_t i, bool dirs) {
   TrackF T;
   T.bad = false;
+  T.fl = FLOOR;
+  T.dfl = 0.f;
+  T.keyed = true;
   const uint2 bz = __ldg(z + i);
   split(__ldg(x + i), T.xh, T.xl, T.bad);
   split(__ldg(y + i), T.yh, T.yl, T.bad);
@@ -185,10 +191,10 @@ __device__ __forceinline__ int decide(const SInt& S, bool& flag) {
 struct Gv { float g, E; };
 
 // |p| - D from split values (the low part may have either sign: |p| = |ph| + sign(ph) pl)
-__device__ __forceinline__ Gv abs_minus(float ph, float pl, float Dh, float Dl) {
+__device__ __forceinline__ Gv abs_minus(float ph, float pl, float Dh, float Dl, float fl) {
   const float a = fabsf(ph);
   const float g = (a - Dh) + ((ph < 0 ? -pl : pl) - Dl);
-  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, a + Dh, FLOOR))};
+  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, a + Dh, fl))};
 }
 // (n.p - c) with n, c split, p split
 __device__ __forceinline__ Gv plane_g(const float* nh, const float* nl, float ch, float cl,
@@ -201,7 +207,7 @@ __device__ __forceinline__ Gv plane_g(const float* nh, const float* nl, float ch
   lo = fmaf(nh[2], T.zl, fmaf(nl[2], T.zh, lo));
   lo -= cl;
   const float g = s3.h + lo;
-  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, fabsf(T.xh) + fabsf(T.yh) + fabsf(T.zh) + fabsf(ch), FLOOR))};
+  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, fabsf(T.xh) + fabsf(T.yh) + fabsf(T.zh) + fabsf(ch), 2.f * T.fl))};
 }
 
 // ------------------------------------------------------------------- box
@@ -212,12 +218,13 @@ __device__ __forceinline__ Gv plane_g(const float* nh, const float* nl, float ch
 // the near face the slab is entered at -b and left at -a, otherwise entered at a
 // and left at b.  DistanceToOut = min exit, DistanceToIn = max entry when it comes
 // before the min exit.
+template <bool FRAME = false>
 __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32& R) {
   const float ph[3] = {T.xh, T.yh, T.zh}, pl[3] = {T.xl, T.yl, T.zl}, d[3] = {T.u, T.v, T.w};
   Gv g[3];
   SInt si = sint();
   for (int i = 0; i < 3; i++) {
-    g[i] = abs_minus(ph[i], pl[i], S.Dh[i], S.Dl[i]);
+    g[i] = abs_minus(ph[i], pl[i], S.Dh[i], S.Dl[i], T.fl);
     si.add(g[i].g, g[i].E);
   }
   const float s = si.s;
@@ -230,13 +237,18 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
   bool miss = false, any_out = false, all_in = true;
   for (int i = 0; i < 3; i++) {
     const bool toward = (ph[i] < 0) == (d[i] < 0);  // toward the face on the point's side
+    if (FRAME && fabsf(d[i]) <= 4.f * T.dfl) R.flag = true;  // sign of d not certain
     if (d[i] == 0) {
       if (fabsf(g[i].g) <= g[i].E) R.flag = true;
       miss |= g[i].g > 0;
     } else {
       const float inv = __frcp_rn(fabsf(d[i]));
       const float a = g[i].g * inv, b = (S.Dh[i] + fabsf(ph[i])) * inv;
-      const Val A{a, fmaf(g[i].E, inv, 5.f * U * fabsf(a))}, B{b, 9.f * U * b};
+      Val A{a, fmaf(g[i].E, inv, 5.f * U * fabsf(a))}, B{b, 9.f * U * b};
+      if (FRAME) {  // error of the direction component
+        A.e = fmaf(1.01f * fabsf(a) * T.dfl, inv, A.e);
+        B.e = fmaf(fmaf(1.01f * b, T.dfl, T.fl), inv, B.e);
+      }
       tn = vmax(tn, toward ? Val{-B.v, B.e} : A);
       tf = vmin(tf, toward ? Val{-A.v, A.e} : B);
     }
@@ -260,7 +272,8 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
         for (int i = 0; i < 3; i++) {
           const float q = fmaf(h, d[i], ph[i]);
           sm = fmaxf(sm, fabsf(q) - S.Dh[i]);
-          em = fmaxf(em, 4.f * U * (fabsf(q) + S.Dh[i]) + fabsf(d[i]) * 0.5f * tf.e);
+          em = fmaxf(em, 4.f * U * (fabsf(q) + S.Dh[i]) + fabsf(d[i]) * 0.5f * tf.e +
+                             (FRAME ? fmaf(h, T.dfl, 2.f * T.fl) : 0.f));
         }
         if (!(tf.v < BIG) || fabsf(sm) <= em + 1e-12f) R.flag = true;
         else if (sm > 0) R.dout = 0.f;
@@ -286,6 +299,7 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
 // One uniform path as for the box: every side plane gives one crossing
 // t = -g / (n.d), an entry when n.d < 0 and an exit when n.d > 0; the z slab
 // gives its two crossings like a box axis.
+template <bool FRAME = false>
 __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R32& R) {
   Gv g[5];
   float gd[5], egd[5];
@@ -293,11 +307,11 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
     g[i] = plane_g(S.plh[i], S.pll[i], S.plh[i][3], S.pll[i][3], T);
     const float a = S.plh[i][0] * T.u, b = S.plh[i][1] * T.v, c = S.plh[i][2] * T.w;
     gd[i] = (a + b) + c;
-    egd[i] = 8.f * U * (fabsf(a) + fabsf(b) + fabsf(c)) + 1e-30f;
+    egd[i] = 8.f * U * (fabsf(a) + fabsf(b) + fabsf(c)) + (FRAME ? 2.f * T.dfl : 0.f) + 1e-30f;
   }
-  g[4] = abs_minus(T.zh, T.zl, S.dzh, S.dzl);
+  g[4] = abs_minus(T.zh, T.zl, S.dzh, S.dzl, T.fl);
   gd[4] = T.zh < 0 ? -T.w : T.w;
-  egd[4] = 0.f;
+  egd[4] = FRAME ? T.dfl : 0.f;
   SInt si = sint();
   for (int i = 0; i < 5; i++) si.add(g[i].g, g[i].E);
   const float s = si.s;
@@ -323,13 +337,18 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
   }
   {  // z slab
     const bool toward = (T.zh < 0) == (T.w < 0);
+    if (FRAME && fabsf(T.w) <= 4.f * T.dfl) R.flag = true;  // sign of w not certain
     if (T.w == 0) {
       if (fabsf(g[4].g) <= g[4].E) R.flag = true;
       miss |= g[4].g > 0;
     } else {
       const float iw = __frcp_rn(fabsf(T.w));
       const float a = g[4].g * iw, b = (S.dzh + fabsf(T.zh)) * iw;
-      const Val A{a, fmaf(g[4].E, iw, 5.f * U * fabsf(a))}, B{b, 9.f * U * b};
+      Val A{a, fmaf(g[4].E, iw, 5.f * U * fabsf(a))}, B{b, 9.f * U * b};
+      if (FRAME) {
+        A.e = fmaf(1.01f * fabsf(a) * T.dfl, iw, A.e);
+        B.e = fmaf(fmaf(1.01f * b, T.dfl, T.fl), iw, B.e);
+      }
       tn = vmax(tn, toward ? Val{-B.v, B.e} : A);
       tf = vmin(tf, toward ? Val{-A.v, A.e} : B);
     }
@@ -358,7 +377,7 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
           sm = fmaxf(sm, v);
           em = fmaxf(em, 8.f * U * (fabsf(qx) + fabsf(qy) + fabsf(qz) + fabsf(P[3])));
         }
-        em += 0.5f * tf.e + 1e-12f;
+        em += 0.5f * tf.e + (FRAME ? fmaf(tf.v, T.dfl, 2.f * T.fl) : 0.f) + 1e-12f;
         if (!(tf.v < BIG) || fabsf(sm) <= em) R.flag = true;
         else if (sm > 0) R.dout = 0.f;
       }
@@ -386,6 +405,7 @@ struct Lat {   // a lateral constraint evaluated in double-float
   float dh, dl;  // r - R in double-float
   float Rh, Rl;  // R = a z + b at the point, double-float
   float scale;   // magnitude of the terms of r - R
+  float ed;      // bound of dh + dl
 };
 
 template <bool TUBE>
@@ -404,9 +424,11 @@ __device__ __forceinline__ Lat lateral(float ah, float al, float bh, float bl, f
   const F2 dd = tsum(rh, -Rh);
   const float dl = dd.l + (rl - Rl);
   const float delta = dd.h + dl;
-  const float eDelta = fmaf(4.f * U, fabsf(delta), fmaf(G42, scale, FLOOR));
+  // coordinate errors: r moves by up to 1.5 fl, a z + b by |a| fl
+  const float ed = fmaf(G42, scale, (2.f + fabsf(ah)) * T.fl);
+  const float eDelta = fmaf(4.f * U, fabsf(delta), ed);
   const float g = outer ? delta * k : -delta * k;
-  return {g, fmaf(4.f * U, fabsf(g), eDelta * k), delta, eDelta, dd.h, dl, Rh, Rl, scale};
+  return {g, fmaf(4.f * U, fabsf(g), eDelta * k), delta, eDelta, dd.h, dl, Rh, Rl, scale, ed};
 }
 
 // phi plane value n.p in double-float
@@ -417,7 +439,7 @@ __device__ __forceinline__ Gv phi_plane(const float* nh, const float* nl, const 
   lo = fmaf(nh[0], T.xl, fmaf(nl[0], T.xh, lo));
   lo = fmaf(nh[1], T.yl, fmaf(nl[1], T.yh, lo));
   const float g = s1.h + lo;
-  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, fabsf(T.xh) + fabsf(T.yh), FLOOR))};
+  return {g, fmaf(4.f * U, fabsf(g), fmaf(G42, fabsf(T.xh) + fabsf(T.yh), 1.5f * T.fl))};
 }
 
 // Crossings of r = a z + b with the track: f(t) = A t^2 + 2 B t + C = r(t)^2 - R(t)^2,
@@ -449,7 +471,7 @@ __device__ __forceinline__ F2 df_norm(float h, float l) {
   return {s, l - (s - h)};
 }
 
-template <bool TUBE>
+template <bool TUBE, bool FRAME>
 __device__ inline Quad quad32(float a, float al, const Lat& L, const TrackF& T, F2 rad, float erad, F2 A0,
                               float rh, float rl) {
   Quad q;
@@ -464,6 +486,7 @@ __device__ inline Quad quad32(float a, float al, const Lat& L, const TrackF& T, 
     Ad = A0;
     eB = erad;
     eA = G42 * A0.h + 1e-30f;
+    if (FRAME) eA = fmaf(2.02f * T.dfl, fabsf(T.u) + fabsf(T.v), eA);
   } else {
     const F2 dd = tprod(a, T.w);
     D = df_norm(dd.h, dd.l + fmaf(a, T.wl, al * T.w));
@@ -476,12 +499,17 @@ __device__ inline Quad quad32(float a, float al, const Lat& L, const TrackF& T, 
     Ad = df_norm(as.h, as.l + (A0.l - fmaf(2.f * D.h, D.l, d2.l)));
     eB = fmaf(2.f * G42 * fabsf(D.h), L.scale + fabsf(L.Rh), erad);
     eA = fmaf(G42, A0.h + d2.h, 1e-30f);
+    if (FRAME) {  // direction errors: A0 by 2 (|u| + |v|) dfl, D by |a| dfl
+      const float eDd = 1.01f * fabsf(a) * T.dfl;
+      eB = fmaf(fabsf(L.Rh) + L.ed, eDd, fmaf(fabsf(D.h), fabsf(a) * T.fl, eB));
+      eA = fmaf(2.02f * T.dfl, fabsf(T.u) + fabsf(T.v), fmaf(2.f * fabsf(D.h) + eDd, eDd, eA));
+    }
   }
   const F2 ps = tsum(rh, L.Rh);
   const F2 Sd = df_norm(ps.h, ps.l + (rl + L.Rl));  // r + P
   const F2 cp = tprod(L.dh, Sd.h);
   const F2 Cd = df_norm(cp.h, cp.l + fmaf(L.dh, Sd.l, L.dl * Sd.h));
-  const float eC = fmaf(fmaf(G42, L.scale, FLOOR), fmaf(2.f, Sd.h, fabsf(L.dh)), 1e-30f);
+  const float eC = fmaf(L.ed, fmaf(2.f, Sd.h, fabsf(L.dh)) + L.ed, 1e-30f);
   const float A = Ad.h, B = Bd.h, C = Cd.h;
   if (A == 0.f && D.h == 0.f && A0.h == 0.f) return q;  // parallel to the axis of a cylinder: no crossing
   const F2 b2 = tprod(Bd.h, Bd.h);
@@ -523,50 +551,6 @@ __device__ inline Quad quad32(float a, float al, const Lat& L, const TrackF& T, 
   return q;
 }
 
-// strict-margin checks of an entry point q = p + t d (error of q: eq per coordinate)
-struct Pt { float x, y, z, e; };
-__device__ __forceinline__ Pt advance(const TrackF& T, Val t) {
-  const float x = fmaf(t.v, T.u, T.xh), y = fmaf(t.v, T.v, T.yh), z = fmaf(t.v, T.w, T.zh);
-  const float e = t.e + 4.f * U * (fabsf(T.xh) + fabsf(T.yh) + fabsf(T.zh) + fabsf(t.v));
-  return {x, y, z, e};
-}
-// Returns +1 if certainly inside the open lateral region of section k, -1 if certainly
-// not, 0 if too close to decide.
-__device__ __forceinline__ int radial_in(const Desc& S, int k, const Pt& q, bool skip_out, bool skip_in) {
-  const float r = sqrtf(q.x * q.x + q.y * q.y);
-  const float er = q.e * 1.5f + 4.f * U * r;
-  int res = 1;
-  if (!skip_out) {
-    const float R = fmaf(S.oah[k], q.z, S.obh[k]);
-    const float m = R - r;
-    const float e = er + fabsf(S.oah[k]) * q.e + 4.f * U * (fabsf(R) + fabsf(S.oah[k] * q.z)) + 1e-30f;
-    if (fabsf(m) <= e) res = 0;
-    else if (m < 0) return -1;
-  }
-  if (!skip_in && ((S.inner >> k) & 1u)) {
-    const float R = fmaf(S.iah[k], q.z, S.ibh[k]);
-    const float m = r - R;
-    const float e = er + fabsf(S.iah[k]) * q.e + 4.f * U * (fabsf(R) + fabsf(S.iah[k] * q.z)) + 1e-30f;
-    if (fabsf(m) <= e) res = 0;
-    else if (m < 0) return -1;
-  }
-  return res;
-}
-__device__ __forceinline__ int phi_in(const Desc& S, const Pt& q) {
-  if (!(S.flags & kHasPhi)) return 1;
-  const float a = S.nsh[0] * q.x + S.nsh[1] * q.y, b = S.neh[0] * q.x + S.neh[1] * q.y;
-  const float e = 1.5f * q.e + 4.f * U * (fabsf(q.x) + fabsf(q.y)) + 1e-30f;
-  const float g = (S.flags & kPhiWide) ? fminf(a, b) : fmaxf(a, b);
-  if (fabsf(g) <= e) return 0;
-  return g < 0 ? 1 : -1;
-}
-// +1 if z0 < q.z < zN and zk <= q.z <= zk1 certainly, -1 if certainly not, 0 otherwise
-__device__ __forceinline__ int zrange_in(float lo, float hi, float z0, float zN, const Pt& q) {
-  const float e = q.e + 4.f * U * fabsf(q.z);
-  if (fabsf(q.z - lo) <= e || fabsf(q.z - hi) <= e || fabsf(q.z - z0) <= e || fabsf(q.z - zN) <= e) return 0;
-  return (q.z >= lo && q.z <= hi && q.z > z0 && q.z < zN) ? 1 : -1;
-}
-
 // ----- interval form of the single-section solids (tube, cone) -----
 // Along the track each constraint holds on an interval (convex regions) whose ends
 // are its crossings; the solid is C minus X1 minus X2 where C is the intersection
@@ -606,11 +590,16 @@ __device__ __forceinline__ Iv iv_and(const Iv& x, const Iv& y) {
 __device__ __forceinline__ int side(Val a, Val b) { return apart(a, b) ? (a.v < b.v ? -1 : 1) : 0; }
 // a crossing certainly after 0; one that is not is at 0+ or before it
 __device__ __forceinline__ bool after0(Val a) { return a.v > a.e; }
-// side(t, b) and side(b, t) where t may be 0+ (z)
-__device__ __forceinline__ int side_tb(Val t, bool z, Val b) { return z ? (after0(b) ? -1 : 1) : side(t, b); }
-__device__ __forceinline__ int side_bt(Val b, Val t, bool z) { return z ? (after0(b) ? 1 : -1) : side(b, t); }
-// Is the point at t (0+ if z) on the open piece lat \ (X1 u X2)?  +1 certainly, -1
-// certainly not, 0 unsure.
+// side(t, b) and side(b, t) where t means "just after" a crossing: 0+ (z), or the crossing
+// equal to t itself, count as passed
+__device__ __forceinline__ int side_tb(Val t, bool z, Val b) {
+  return z ? (after0(b) ? -1 : 1) : (b.v == t.v ? 1 : side(t, b));
+}
+__device__ __forceinline__ int side_bt(Val b, Val t, bool z) {
+  return z ? (after0(b) ? 1 : -1) : (b.v == t.v ? -1 : side(b, t));
+}
+// Is the point just after t (0+ if z) on the open piece lat \ (X1 u X2)?  +1 certainly,
+// -1 certainly not, 0 unsure.
 __device__ __forceinline__ int in_piece(const Iv& lat, const Iv& X1, const Iv& X2, Val t, bool z) {
   if (lat.empty) return -1;
   const int a = side_bt(lat.lo, t, z), b = side_tb(t, z, lat.hi);
@@ -651,7 +640,7 @@ __device__ __forceinline__ bool inside_estimate(const Desc& S, const uint2* x, c
   return true;
 }
 
-template <bool TUBE>
+template <bool TUBE, bool FRAME = false>
 __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32& R) {
   const int nz = S.nz, last = nz - 1;
   // r = sqrt(x^2 + y^2) in double-float
@@ -665,17 +654,29 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
     const F2 rr = tprod(rh, rh);
     rl = (((r2h - rr.h) - rr.l) + r2l) * __fdividef(0.5f, rh);
   }
+  // Section of the point: the first k with z < z[k+1].  In a placed volume's frame the
+  // binary64 z is not at hand: a point within rounding of an internal plane goes to binary64.
   int k0 = 0;
-  while (k0 < nz - 2 && T.zkey >= S.zkey[k0 + 1]) k0++;
+  bool near_plane = false;
+  if (!FRAME) {
+    while (k0 < nz - 2 && T.zkey >= S.zkey[k0 + 1]) k0++;
+  } else {
+    while (k0 < nz - 2 && (T.zh - S.zh[k0 + 1]) + (T.zl - S.zl[k0 + 1]) >= 0.f) k0++;
+    for (int j = k0; j <= k0 + 1; j++) {
+      if (j < 1 || j > nz - 2) continue;
+      const float gj = (T.zh - S.zh[j]) + (T.zl - S.zl[j]);
+      near_plane |= fabsf(gj) <= fmaf(G42, fabsf(T.zh) + fabsf(S.zh[j]), 2.f * T.fl);
+    }
+  }
   const bool has_phi = S.flags & kHasPhi, wide = S.flags & kPhiWide;
   const bool has_in = (S.inner >> k0) & 1u;
   const Lat lo_ = lateral<TUBE>(S.oah[k0], S.oal[k0], S.obh[k0], S.obl[k0], S.ok_[k0], rh, rl, T, true);
   Lat li_{-F_INF, 0.f, 0.f, 0.f};
   if (has_in) li_ = lateral<TUBE>(S.iah[k0], S.ial[k0], S.ibh[k0], S.ibl[k0], S.ik_[k0], rh, rl, T, false);
   const float gz0 = (S.zh[0] - T.zh) + (S.zl[0] - T.zl);
-  const float Ez0 = 4.f * U * fabsf(gz0) + G42 * (fabsf(T.zh) + fabsf(S.zh[0])) + FLOOR;
+  const float Ez0 = 4.f * U * fabsf(gz0) + G42 * (fabsf(T.zh) + fabsf(S.zh[0])) + T.fl;
   const float gz1 = (T.zh - S.zh[last]) + (T.zl - S.zl[last]);
-  const float Ez1 = 4.f * U * fabsf(gz1) + G42 * (fabsf(T.zh) + fabsf(S.zh[last])) + FLOOR;
+  const float Ez1 = 4.f * U * fabsf(gz1) + G42 * (fabsf(T.zh) + fabsf(S.zh[last])) + T.fl;
   Gv pa{-F_INF, 0.f}, pb{-F_INF, 0.f};
   float gphi = -F_INF, phlo = -F_INF, phhi = -F_INF;  // phi value and the interval holding it
   if (has_phi) {
@@ -699,6 +700,7 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
   if (has_phi) si.add_int(gphi, phlo, phhi);
   const float s = si.s;
   R.code = decide(si, R.flag);
+  if (FRAME && near_plane) R.flag = true;
 
   if (want & (kWantSin | kWantSout)) {
     R.sin = R.code == 0 ? -1.f : (R.code == 1 ? 0.f : s);
@@ -720,17 +722,17 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
           }
           const float gk0 = (S.zh[k] - T.zh) + (S.zl[k] - T.zl);
           const float gk1 = (T.zh - S.zh[k + 1]) + (T.zl - S.zl[k + 1]);
-          c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + FLOOR);
-          c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + FLOOR);
+          c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + T.fl);
+          c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + T.fl);
         } else {
           const float go = (rh - fmaf(S.oah[k], T.zh, S.obh[k])) * S.ok_[k];
-          c.add(go, 8.f * U * (rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k])));
+          c.add(go, fmaf(8.f * U, rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k]), 3.f * T.fl));
           if ((S.inner >> k) & 1u) {
             const float gi2 = (fmaf(S.iah[k], T.zh, S.ibh[k]) - rh) * S.ik_[k];
-            c.add(gi2, 8.f * U * (rh + fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k])));
+            c.add(gi2, fmaf(8.f * U, rh + fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k]), 3.f * T.fl));
           }
-          c.add(S.zh[k] - T.zh, 4.f * U * (fabsf(T.zh) + fabsf(S.zh[k])));
-          c.add(T.zh - S.zh[k + 1], 4.f * U * (fabsf(T.zh) + fabsf(S.zh[k + 1])));
+          c.add(S.zh[k] - T.zh, fmaf(4.f * U, fabsf(T.zh) + fabsf(S.zh[k]), T.fl));
+          c.add(T.zh - S.zh[k + 1], fmaf(4.f * U, fabsf(T.zh) + fabsf(S.zh[k + 1]), T.fl));
         }
         if (has_phi) c.add_int(gphi, phlo, phhi);
         if (R.code == 0 && k == k0) {
@@ -749,8 +751,8 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
           const float go = (rh - fmaf(S.oah[k], T.zh, S.obh[k])) * S.ok_[k];
           float v = fmaxf(go, fmaxf(S.zh[k] - T.zh, T.zh - S.zh[k + 1]));
           if ((S.inner >> k) & 1u) v = fmaxf(v, (fmaf(S.iah[k], T.zh, S.ibh[k]) - rh) * S.ik_[k]);
-          const float ev = 8.f * U * (rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k]) + fabsf(T.zh) + fabsf(S.zh[k]) +
-                                      fabsf(S.zh[k + 1]) + fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k]));
+          const float ev = fmaf(8.f * U, rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k]) + fabsf(T.zh) + fabsf(S.zh[k]) +
+                                      fabsf(S.zh[k + 1]) + fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k]), 3.f * T.fl);
           if (!near && v - ev > best.v + best.e) continue;  // cannot be the minimum
           const Lat lo2 = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
           c.add(lo2.g, lo2.E);
@@ -760,8 +762,8 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
           }
           const float gk0 = (S.zh[k] - T.zh) + (S.zl[k] - T.zl);
           const float gk1 = (T.zh - S.zh[k + 1]) + (T.zl - S.zl[k + 1]);
-          c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + FLOOR);
-          c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + FLOOR);
+          c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + T.fl);
+          c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + T.fl);
           if (has_phi) c.add_int(gphi, phlo, phhi);
           best2 = vmin(best2, {c.s, c.err()});
         }
@@ -777,15 +779,20 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
 
   const F2 rad = radial_df(T);
   const float radial = rad.h;
-  const float eRadial = 4.f * U * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;
-  const float erad = G42 * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;  // of rad
+  float erad = G42 * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;  // of rad
+  float eRadial = 4.f * U * (fabsf(T.xh * T.u) + fabsf(T.yh * T.v)) + 1e-30f;
+  if (FRAME) {  // point and direction errors of a frame track
+    const float ef = fmaf(1.01f * T.dfl, fabsf(T.xh) + fabsf(T.yh), 1.01f * T.fl * (fabsf(T.u) + fabsf(T.v)));
+    erad += ef;
+    eRadial += ef;
+  }
   const F2 A0 = a0_df(T);
   float nds = 0.f, nde = 0.f, ends = 0.f, ende = 0.f;
   if (has_phi) {
     nds = S.nsh[0] * T.u + S.nsh[1] * T.v;
     nde = S.neh[0] * T.u + S.neh[1] * T.v;
-    ends = 6.f * U * (fabsf(S.nsh[0] * T.u) + fabsf(S.nsh[1] * T.v)) + 1e-30f;
-    ende = 6.f * U * (fabsf(S.neh[0] * T.u) + fabsf(S.neh[1] * T.v)) + 1e-30f;
+    ends = 6.f * U * (fabsf(S.nsh[0] * T.u) + fabsf(S.nsh[1] * T.v)) + (FRAME ? 1.5f * T.dfl : 0.f) + 1e-30f;
+    ende = 6.f * U * (fabsf(S.neh[0] * T.u) + fabsf(S.neh[1] * T.v)) + (FRAME ? 1.5f * T.dfl : 0.f) + 1e-30f;
   }
   // surface start: decided here only when some constraint certainly grows (leaving)
   // or every one certainly shrinks (entering); the other surface cases go to binary64.
@@ -800,10 +807,11 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
       }
     };
     const float ao = TUBE ? 0.f : S.oah[k0], ai = TUBE ? 0.f : S.iah[k0];
-    add(lo_.g, lo_.E, radial - ao * T.w * rh, eRadial + 4.f * U * fabsf(ao * T.w * rh));
-    if (has_in) add(li_.g, li_.E, -(radial - ai * T.w * rh), eRadial + 4.f * U * fabsf(ai * T.w * rh));
-    add(gz0, Ez0, -T.w, 0.f);
-    add(gz1, Ez1, T.w, 0.f);
+    const float ew = FRAME ? T.dfl : 0.f;
+    add(lo_.g, lo_.E, radial - ao * T.w * rh, eRadial + 4.f * U * fabsf(ao * T.w * rh) + fabsf(ao) * rh * ew);
+    if (has_in) add(li_.g, li_.E, -(radial - ai * T.w * rh), eRadial + 4.f * U * fabsf(ai * T.w * rh) + fabsf(ai) * rh * ew);
+    add(gz0, Ez0, -T.w, ew);
+    add(gz1, Ez1, T.w, ew);
     if (has_phi) {
       if (wide) {
         if (fabsf(pa.g - pb.g) <= pa.E + pb.E) unsure = true;
@@ -815,11 +823,10 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
     }
   }
 
-  // A surface point that is leaving is outside just after 0 (written 0+): DistanceToOut
-  // is 0 and DistanceToIn the first entry after 0+; one that is entering is inside at 0+:
-  // DistanceToIn is 0 and DistanceToOut the end of the stretch holding 0+.  In the
-  // searches below a crossing at 0+ is one not certainly after 0 (it is the surface the
-  // point is on); a result that stays at 0+ contradicts the motion and is flagged.
+  // A surface point that is leaving has DistanceToOut 0 and needs DistanceToIn; one that
+  // is entering has DistanceToIn 0 and needs DistanceToOut.  Both searches below start
+  // just after 0 (written 0+), where a crossing not certainly after 0 is the surface the
+  // point is on.
   const bool surf = R.code == 1;
   const bool leaving = surf && any_out && !unsure, entering = surf && all_in && !unsure;
   if (surf) {
@@ -836,10 +843,17 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
   // Distances in interval form, over the sections the ray meets for t >= 0 in t order.
   // In section k the ray is inside the solid on C \ (X1 u X2): C = outer region of the
   // section's line ∩ the section's z slab ∩ narrow phi, X1 = its hole, X2 = the wedge cut
-  // out by a wide phi.  DistanceToIn (outside point) is the first start of such a piece;
-  // DistanceToOut (inside point) follows the stretch that holds the current point, across
-  // internal planes (not surfaces), to its first lateral or end-plane exit.  Inside and
-  // outside tracks run the same loop body.
+  // out by a wide phi.  Each track computes one distance with two steps: SEARCH finds the
+  // first start of such a piece after tcur; STRETCH follows the piece holding tcur across
+  // internal planes (not surfaces: the profile is continuous) to its end.
+  //   DistanceToIn, outside point:   SEARCH from 0; the start found is the answer.
+  //   DistanceToIn, leaving surface: SEARCH from 0+; if 0+ is itself on a piece (the point
+  //     is inside by less than h), STRETCH to its end and SEARCH again from there.
+  //   DistanceToOut, inside point:   STRETCH from 0; its end is the answer.
+  //   DistanceToOut, entering surface: SEARCH from 0+ (0+ itself, or a start just after 0
+  //     when the point is outside by less than h), then STRETCH; none found: 0.
+  // A value tcur always means "just after that crossing": a crossing equal to it (the same
+  // one) counts as passed.  Inside and outside tracks run the same loop body.
   bool u = false;
   Iv PH = iv_all(), X2 = iv_none();
   if (has_phi) {
@@ -851,24 +865,50 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
   auto plane_t = [&](int j) -> Val {
     const float num = (S.zh[j] - T.zh) + (S.zl[j] - T.zl);
     const float t = num * iw;
-    return {t, fmaf(5.f * U, fabsf(t), fmaf(G42, fabsf(T.zh) + fabsf(S.zh[j]), FLOOR) * fabsf(iw))};
+    float e = fmaf(G42, fabsf(T.zh) + fabsf(S.zh[j]), T.fl);
+    if (FRAME) e = fmaf(1.01f * fabsf(t), T.dfl, e);
+    return {t, fmaf(5.f * U, fabsf(t), e * fabsf(iw))};
   };
   int k, step;
   bool in_range = true;  // for w == 0: the ray's z inside [z0, zN]
-  if (T.w > 0) { step = 1; k = (T.zkey < S.zkey[0]) ? 0 : k0; }
-  else if (T.w < 0) { step = -1; k = (T.zkey > S.zkey[last]) ? last - 1 : k0; }
+  if (FRAME && fabsf(T.w) <= 4.f * T.dfl) u = true;  // the order of the sections is not certain
+  // below z0 (above zN) the first section is k0 = 0 (k0 = nz - 2) already
+  if (T.w > 0) { step = 1; k = k0; }
+  else if (T.w < 0) { step = -1; k = k0; }
   else {  // the ray stays in the plane z = const: one section or none
     step = 0; k = k0;
     in_range = !(gz0 > 0) && !(gz1 > 0);
     for (int j = k0; j <= k0 + 1; j++) {  // on a plane the pieces on both sides meet: binary64
       const float gj = (S.zh[j] - T.zh) + (S.zl[j] - T.zl);
-      if (fabsf(gj) <= 4.f * U * fabsf(gj) + G42 * (fabsf(T.zh) + fabsf(S.zh[j])) + FLOOR) u = true;
+      if (fabsf(gj) <= 4.f * U * fabsf(gj) + G42 * (fabsf(T.zh) + fabsf(S.zh[j])) + T.fl) u = true;
     }
   }
+  // An outside track looks only for an entry: while searching it passes over the sections
+  // whose slab the ray crosses (t >= 0) farther from the axis than the section's largest
+  // outer radius, by a wide margin; a section not certainly missed is examined in full.
+  auto may_enter = [&](int j) -> bool {
+    const float t0 = plane_t(j).v, t1 = plane_t(j + 1).v;
+    const float m = fmaf(1e-5f, fabsf(t0) + fabsf(t1), 1e-6f);
+    const float lo = fmaxf(fminf(t0, t1) - m, 0.f), hi = fmaxf(t0, t1) + m;
+    if (hi < lo) return false;  // behind the start
+    const float tm = fminf(fmaxf(A0.h > 0.f ? -radial / A0.h : lo, lo), hi);
+    const float r2 = fmaf(fmaf(A0.h, tm, 2.f * radial), tm, r2h);
+    const float Rm = fmaxf(fmaf(S.oah[j], S.zh[j], S.obh[j]), fmaf(S.oah[j], S.zh[j + 1], S.obh[j]));
+    const float mag = r2h + 2.f * fabsf(radial * tm) + A0.h * tm * tm + Rm * Rm;
+    return !(r2 - Rm * Rm > fmaf(1e-5f, mag, 1e-6f));
+  };
+  enum { kSearch, kStretch, kDone };
+  const bool goal_out = need_out;
+  int st = R.code == 0 ? kStretch : kSearch;
   Val tcur{0.f, 0.f};
-  bool out_done = !need_out, in_done = !need_in;
-  Val dout{BIG, 0.f}, din{BIG, 0.f};
-  for (int guard = 0; guard < kMaxZ && !(out_done && in_done); guard++) {
+  bool zc = surf;   // tcur is 0+
+  Val ans{BIG, 0.f};
+  bool answered = false;
+  for (int guard = 0; guard < kMaxZ && st != kDone; guard++) {
+    if (step != 0 && st == kSearch && S.nz > 2) {
+      while (k >= 0 && k <= last - 1 && !may_enter(k)) k += step;
+      if (k < 0 || k > last - 1) break;
+    }
     Iv slab = iv_all();
     if (step != 0) {
       const Val ta = plane_t(k), tb = plane_t(k + 1);
@@ -880,69 +920,98 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
     if (!beyond) {
       const float ao = TUBE ? 0.f : S.oah[k];
       const Lat Lo = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
-      const Quad qo = quad32<TUBE>(ao, TUBE ? 0.f : S.oal[k], Lo, T, rad, erad, A0, rh, rl);
+      const Quad qo = quad32<TUBE, FRAME>(ao, TUBE ? 0.f : S.oal[k], Lo, T, rad, erad, A0, rh, rl);
       u |= qo.unsure;
       const Iv lat = iv_and(iv_region(qo, Lo.g, Lo.E, u), PH);  // lateral and phi part of C
       Iv X1 = iv_none();
       if ((S.inner >> k) & 1u) {
         const float ai = TUBE ? 0.f : S.iah[k];
         const Lat Li = k == k0 ? li_ : lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], rh, rl, T, false);
-        const Quad qi = quad32<TUBE>(ai, TUBE ? 0.f : S.ial[k], Li, T, rad, erad, A0, rh, rl);
+        const Quad qi = quad32<TUBE, FRAME>(ai, TUBE ? 0.f : S.ial[k], Li, T, rad, erad, A0, rh, rl);
         u |= qi.unsure;
         X1 = iv_region(qi, -Li.g, Li.E, u);
         if (!X1.empty && !(X1.lo.v < X1.hi.v)) X1 = iv_none();
       }
       const Iv C = iv_and(lat, slab);
-      // first point of C \ (X1 u X2) at t >= 0 (after 0+ for a leaving surface point)
-      if (!in_done && !C.empty && !(leaving && !after0(C.hi))) {
-        bool z = false;  // t is 0+
-        Val t = C.lo;
-        if (leaving ? !after0(C.lo) : !(C.lo.v > 0.f)) { t = Val{0.f, 0.f}; z = leaving; }
+      // v at or before tcur (passed): the same crossing, certainly earlier, or within 0+
+      auto passed = [&](Val v) -> bool {
+        if (zc) return !after0(v);
+        if (v.v == tcur.v) return true;
+        return !lt_sure(tcur, v, u);
+      };
+      // SEARCH: the first point of C \ (X1 u X2) after tcur in this section
+      auto search = [&]() {
+        if (C.empty || passed(C.hi)) return;
+        Val t = tcur;
+        bool z = zc;
+        if (!passed(C.lo)) { t = C.lo; z = false; }
         for (int pass = 0; pass < 2; pass++) {
           const Iv* X[2] = {&X1, &X2};
           for (int j = 0; j < 2; j++) {
             if (X[j]->empty || (!z && t.v == X[j]->hi.v)) continue;
-            const bool after_lo = z ? !after0(X[j]->lo) : !lt_sure(t, X[j]->lo, u);
-            const bool before_hi = z ? after0(X[j]->hi) : lt_sure(t, X[j]->hi, u);
-            if (after_lo && before_hi) { t = X[j]->hi; z = false; }
+            const bool lo_passed = z ? !after0(X[j]->lo) : (X[j]->lo.v == t.v || !lt_sure(t, X[j]->lo, u));
+            const bool hi_ahead = z ? after0(X[j]->hi) : lt_sure(t, X[j]->hi, u);
+            if (lo_passed && hi_ahead) { t = X[j]->hi; z = false; }
           }
         }
-        if (z || lt_sure(t, C.hi, u)) {
-          if (!(t.v > t.e)) u = true;  // entry strictly after 0 (or 0+)
-          din = t;
-          in_done = true;
+        if (!z && (t.v == C.hi.v || !lt_sure(t, C.hi, u))) return;  // pushed past C
+        if (!goal_out && !z) {  // an entry: the answer
+          if (!surf && !(t.v > t.e)) u = true;  // an outside point enters strictly after 0
+          ans = t;
+          answered = true;
+          st = kDone;
+          return;
         }
-      }
-      if (!out_done) {
-        // The section must hold tcur on its open piece.
-        const bool z = entering && guard == 0;  // tcur is 0+
-        const int at = in_piece(lat, X1, X2, tcur, z);
+        st = kStretch;  // DistanceToOut from the piece's start, or a leaving point inside at 0+
+        tcur = t;
+        zc = z;
+      };
+      if (st == kSearch) search();
+      if (st == kStretch) {
+        const int at = in_piece(lat, X1, X2, tcur, zc);
         Val e = lat.hi;  // end of the inside stretch holding tcur
-        if (!X1.empty && (z ? after0(X1.lo) : X1.lo.v > tcur.v)) e = vmin(e, X1.lo);
-        if (!X2.empty && (z ? after0(X2.lo) : X2.lo.v > tcur.v)) e = vmin(e, X2.lo);
-        if (at <= 0) {  // the profile is continuous: the stretch holds tcur unless too close to tell
+        if (!X1.empty && (zc ? after0(X1.lo) : X1.lo.v > tcur.v)) e = vmin(e, X1.lo);
+        if (!X2.empty && (zc ? after0(X2.lo) : X2.lo.v > tcur.v)) e = vmin(e, X2.lo);
+        if (at <= 0) {  // the section must hold tcur (the profile is continuous)
           u = true;
-          out_done = true;
+          st = kDone;
         } else if (step != 0 && lt_sure(slab.hi, e, u)) {  // reaches the far plane first
           const bool end_plane = (step > 0 && k + 1 == last) || (step < 0 && k == 0);
-          if (end_plane) { dout = slab.hi; out_done = true; }
-          else tcur = slab.hi;
-        } else {
-          dout = e;
-          out_done = true;
+          if (!end_plane) {
+            tcur = slab.hi;
+            zc = false;
+          } else if (goal_out) {
+            ans = slab.hi;
+            answered = true;
+            st = kDone;
+          } else {
+            st = kDone;  // leaves through an end plane: no entry after it
+          }
+        } else if (goal_out) {
+          ans = e;
+          answered = true;
+          st = kDone;
+        } else {  // a leaving point's stretch ends: look for the next entry
+          tcur = e;
+          zc = false;
+          st = kSearch;
+          search();
         }
       }
     }
     k += step;
     if (step == 0 || k < 0 || k > last - 1) break;
   }
+  if (st == kStretch) u = true;  // a stretch must end at a surface
   if (need_out) {
-    if (!out_done || u || !certified(dout)) R.flag = true;
-    R.dout = unbig(dout.v);
+    // entering surface point whose ray never gets inside: 0
+    const Val d = answered ? ans : Val{0.f, 0.f};
+    if (u || !certified(d)) R.flag = true;
+    R.dout = unbig(d.v);
   }
   if (need_in) {
-    if (u || !certified(din)) R.flag = true;
-    R.din = in_done ? din.v : F_INF;
+    if (u || !certified(ans)) R.flag = true;
+    R.din = answered ? ans.v : F_INF;
   }
 }
 
