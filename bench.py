@@ -133,6 +133,32 @@ def cpu_baseline(tracks_per_solid: dict, sample: int):
             "sample": f"first {sample} tracks of each of the 5 solids' 2^24-track baskets, all five queries"}
 
 
+def cpu_baseline_sweep(max_exp: int = 16):
+    """The oracle on the sweep's tracks for N <= 2^max_exp, one core and all cores
+    (DistanceToOut only), for the GPU-over-CPU ratio of the paper's figure."""
+    import oracle
+    threads = os.cpu_count() or 1
+    res = {}
+    for name, spec in SWEEP_SPECS:
+        o = oracle.Solid.from_spec(spec)
+        rows = []
+        for e in SWEEP_EXPONENTS:
+            if e > max_exp:
+                break
+            n = 1 << e
+            tr = sweep_tracks(spec, n)
+            row = {"n": n}
+            for label, th in (("1core", 1), ("allcores", threads)):
+                reps = max(1, min(200, (1 << 14) // n))
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    o.query(**tr, threads=th, want=("dist_out",))
+                row[f"oracle_{label}_tracks_per_s"] = n * reps / (time.perf_counter() - t0)
+            rows.append(row)
+        res[name] = rows
+    return {"cores": threads, "rows": res}
+
+
 def gen_inputs(n: int):
     return {name: W.tracks_for_solid(spec, n, seed=2) for name, spec in specs()}
 
@@ -271,12 +297,17 @@ def run_ours(args):
         # release the precision-form buffers before the other forms
         del dev, outs
         torch.cuda.empty_cache()
+        line["box1024"] = bench_box1024(gv, torch)
+        line["fp64_tube_cone_2e20"] = bench_fp64_m2(gv, torch, peaks)
+        line["sweep_dist_out"] = bench_sweep(gv, torch)
         line["batched"] = bench_batched(gv, torch, max(3, args.steps), peaks)
         line["nav"] = bench_nav(gv, torch, max(3, args.steps))
         if rank == 0:
             line["serving"] = bench_serving(gv, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(inputs, args.cpu_sample)
+        if not args.no_extra:
+            line["sweep_dist_out_oracle"] = cpu_baseline_sweep()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -341,6 +372,93 @@ def _timed(torch, fn, reps):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+SWEEP_EXPONENTS = tuple(range(4, 25, 2))  # N = 2^4 ... 2^24
+SWEEP_SPECS = (("box", W.BOX_M1), ("tube", W.TUBE_M2))
+
+
+def sweep_tracks(spec, n):
+    """The paper's experiment: points inside the solid, isotropic directions."""
+    return W.tracks_for_solid(spec, n, seed=6637, near_frac=0.0, inside_frac=1.0)
+
+
+def bench_sweep(gv, torch):
+    """The paper's measurement (its one figure): Box and Tube DistanceToOut throughput
+    against the number of tracks N, for points inside with isotropic directions.  Per N
+    the mean device time of one gv_query call over many repetitions (about 2^26 tracks
+    per N in total, at least 8 calls), and for N <= 2^16 one call replayed from a CUDA
+    graph as well."""
+    res = {}
+    nmax = 1 << max(SWEEP_EXPONENTS)
+    for name, spec in SWEEP_SPECS:
+        dev = {k: torch.from_numpy(v).cuda() for k, v in sweep_tracks(spec, nmax).items()}
+        s = gv.Solid.from_spec(spec)
+        ws = gv.Workspace(nmax)
+        dout = torch.empty(nmax, dtype=torch.float64, device="cuda")
+        rows = []
+        for e in SWEEP_EXPONENTS:
+            n = 1 << e
+            sub = {k: v[:n] for k, v in dev.items()}
+            out = {"dist_out": dout[:n]}
+            reps = max(8, min(5000, (1 << 26) // n))
+            row = {"n": n}
+            for prec in ("fp32_refine", "fp64"):
+                ms = _timed(torch, lambda: gv.query(s, sub, precision=prec, out=out, workspace=ws), reps)
+                row[prec + "_tracks_per_s"] = n / (ms * 1e-3)
+                row[prec + "_us_per_call"] = ms * 1e3
+            if n <= 1 << 16:
+                stream = torch.cuda.Stream()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.stream(stream):
+                    gv.query(s, sub, precision="fp32_refine", out=out, workspace=ws, stream=stream)
+                    torch.cuda.synchronize()
+                    with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                        gv.query(s, sub, precision="fp32_refine", out=out, workspace=ws, stream=stream)
+                ms = _timed(torch, g.replay, reps)
+                row["fp32_refine_graph_us_per_call"] = ms * 1e3
+            rows.append(row)
+        res[name] = rows
+    return res
+
+
+def bench_box1024(gv, torch, reps=5000):
+    """1024 tracks against the (10,20,30) box, all five queries: a launch-latency bound
+    basket; mean time per gv_query call and per replay of a captured call."""
+    tr = W.box1024()
+    dev = {k: torch.from_numpy(v).cuda() for k, v in tr.items()}
+    s = gv.Solid.from_spec(W.BOX_M1)
+    ws = gv.Workspace(1024)
+    out = gv.alloc_results(1024, "cuda")
+    res = {"workload": "box (10,20,30), 1024 tracks, 5% within 1e-10 mm of a face, all five queries"}
+    for prec in ("fp32_refine", "fp64"):
+        res[prec + "_us_per_call"] = 1e3 * _timed(
+            torch, lambda: gv.query(s, dev, precision=prec, out=out, workspace=ws), reps)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        gv.query(s, dev, precision="fp32_refine", out=out, workspace=ws, stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+            gv.query(s, dev, precision="fp32_refine", out=out, workspace=ws, stream=stream)
+    res["fp32_refine_graph_us_per_call"] = 1e3 * _timed(torch, g.replay, reps)
+    return res
+
+
+def bench_fp64_m2(gv, torch, peaks, reps=20):
+    """Tube (5,20,30,0,270 deg) and cone (0,10,5,25,40,0,360 deg), 2^20 tracks each, plain
+    binary64, all five queries (the binary64 kernels alone, against the HBM roof)."""
+    res = {}
+    n = 1 << 20
+    for name, spec in (("tube", W.TUBE_M2), ("cone", W.CONE_M2)):
+        dev = {k: torch.from_numpy(v).cuda() for k, v in W.tracks_for_solid(spec, n, seed=8).items()}
+        s = gv.Solid.from_spec(spec)
+        out = gv.alloc_results(n, "cuda")
+        ms = _timed(torch, lambda: gv.query(s, dev, precision="fp64", out=out), reps)
+        gbs = n * BYTES_PER_TRACK / (ms * 1e-3) / 1e9
+        res[name] = {"queries_per_s": n * N_QUERIES / (ms * 1e-3), "us": ms * 1e3, "hbm_gbs": gbs,
+                     "hbm_frac": gbs / peaks["hbm_gbs"]}
+    return res
 
 
 def bench_batched(gv, torch, reps, peaks):

@@ -707,69 +707,60 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
     R.sout = R.code == 2 ? -1.f : (R.code == 1 ? 0.f : -s);
     if (nz == 2 && R.code != 1 && !certified({fabsf(s), si.err()})) R.flag = true;
     if (nz > 2 && R.code != 1) {
-      // sections as closed pieces: the containing one and its neighbours in
-      // double-float, the others in plain binary32 with their bounds
-      Val best{F_INF, 0.f};
-      const int kb = R.code == 0 ? k0 : 0, ke = R.code == 0 ? k0 + 1 : last;
-      for (int k = kb; k < ke; k++) {
+      // sections as closed pieces (own z-planes included), each a max of constraints
+      auto closed_df = [&](int k) -> Val {
         SInt c = sint();
-        if (k >= k0 - 1 && k <= k0 + 1) {
-          const Lat lo2 = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
-          c.add(lo2.g, lo2.E);
-          if ((S.inner >> k) & 1u) {
-            const Lat li2 = k == k0 ? li_ : lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], rh, rl, T, false);
-            c.add(li2.g, li2.E);
-          }
-          const float gk0 = (S.zh[k] - T.zh) + (S.zl[k] - T.zl);
-          const float gk1 = (T.zh - S.zh[k + 1]) + (T.zl - S.zl[k + 1]);
-          c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + T.fl);
-          c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + T.fl);
-        } else {
-          const float go = (rh - fmaf(S.oah[k], T.zh, S.obh[k])) * S.ok_[k];
-          c.add(go, fmaf(8.f * U, rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k]), 3.f * T.fl));
-          if ((S.inner >> k) & 1u) {
-            const float gi2 = (fmaf(S.iah[k], T.zh, S.ibh[k]) - rh) * S.ik_[k];
-            c.add(gi2, fmaf(8.f * U, rh + fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k]), 3.f * T.fl));
-          }
-          c.add(S.zh[k] - T.zh, fmaf(4.f * U, fabsf(T.zh) + fabsf(S.zh[k]), T.fl));
-          c.add(T.zh - S.zh[k + 1], fmaf(4.f * U, fabsf(T.zh) + fabsf(S.zh[k + 1]), T.fl));
+        const Lat lo2 = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
+        c.add(lo2.g, lo2.E);
+        if ((S.inner >> k) & 1u) {
+          const Lat li2 = k == k0 ? li_ : lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], rh, rl, T, false);
+          c.add(li2.g, li2.E);
         }
+        const float gk0 = (S.zh[k] - T.zh) + (S.zl[k] - T.zl);
+        const float gk1 = (T.zh - S.zh[k + 1]) + (T.zl - S.zl[k + 1]);
+        c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + T.fl);
+        c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + T.fl);
         if (has_phi) c.add_int(gphi, phlo, phhi);
-        if (R.code == 0 && k == k0) {
-          R.sout = -c.s;
-          if (!certified({c.s < 0 ? -c.s : c.s, c.err()})) R.flag = true;
-          break;
-        }
-        best = vmin(best, {c.s, c.err()});
-      }
-      if (R.code == 2 && !certified(best)) {
-        // far sections whose plain bounds may still hold the minimum: redo them in double-float
-        Val best2{BIG, 0.f};
-        for (int k = 0; k < last; k++) {
-          SInt c = sint();
-          const bool near = k >= k0 - 1 && k <= k0 + 1;
-          const float go = (rh - fmaf(S.oah[k], T.zh, S.obh[k])) * S.ok_[k];
-          float v = fmaxf(go, fmaxf(S.zh[k] - T.zh, T.zh - S.zh[k + 1]));
-          if ((S.inner >> k) & 1u) v = fmaxf(v, (fmaf(S.iah[k], T.zh, S.ibh[k]) - rh) * S.ik_[k]);
-          const float ev = fmaf(8.f * U, rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k]) + fabsf(T.zh) + fabsf(S.zh[k]) +
-                                      fabsf(S.zh[k + 1]) + fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k]), 3.f * T.fl);
-          if (!near && v - ev > best.v + best.e) continue;  // cannot be the minimum
-          const Lat lo2 = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
-          c.add(lo2.g, lo2.E);
+        return {c.s, c.err()};
+      };
+      if (R.code == 0) {  // SafetyToOut: the containing piece
+        const Val c = closed_df(k0);
+        R.sout = -c.v;
+        if (!certified({fabsf(c.v), c.e})) R.flag = true;
+      } else {
+        // SafetyToIn = min over pieces.  Plain binary32 values with their bounds give an
+        // upper bound umin on the minimum; only pieces whose lower bound is below it can
+        // hold it, and only those are evaluated in double-float (each lane loops over its
+        // own candidates, one or two as a rule).
+        auto closed_f = [&](int k, float& e) -> float {
+          float v = fmaxf((rh - fmaf(S.oah[k], T.zh, S.obh[k])) * S.ok_[k], fmaxf(S.zh[k] - T.zh, T.zh - S.zh[k + 1]));
+          float m = rh + fabsf(S.oah[k] * T.zh) + fabsf(S.obh[k]) + fabsf(T.zh) + fabsf(S.zh[k]) + fabsf(S.zh[k + 1]);
           if ((S.inner >> k) & 1u) {
-            const Lat li2 = k == k0 ? li_ : lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], rh, rl, T, false);
-            c.add(li2.g, li2.E);
+            v = fmaxf(v, (fmaf(S.iah[k], T.zh, S.ibh[k]) - rh) * S.ik_[k]);
+            m += fabsf(S.iah[k] * T.zh) + fabsf(S.ibh[k]);
           }
-          const float gk0 = (S.zh[k] - T.zh) + (S.zl[k] - T.zl);
-          const float gk1 = (T.zh - S.zh[k + 1]) + (T.zl - S.zl[k + 1]);
-          c.add(gk0, 4.f * U * fabsf(gk0) + G42 * (fabsf(T.zh) + fabsf(S.zh[k])) + T.fl);
-          c.add(gk1, 4.f * U * fabsf(gk1) + G42 * (fabsf(T.zh) + fabsf(S.zh[k + 1])) + T.fl);
-          if (has_phi) c.add_int(gphi, phlo, phhi);
-          best2 = vmin(best2, {c.s, c.err()});
+          e = fmaf(8.f * U, m, 3.f * T.fl);
+          if (has_phi) { v = fmaxf(v, gphi); e += phhi - phlo; }
+          return v;
+        };
+        float umin = F_INF;
+        for (int k = 0; k < last; k++) {
+          float e;
+          const float v = closed_f(k, e);
+          umin = fminf(umin, v + e);
         }
-        best = best2;
-      }
-      if (R.code == 2) {
+        uint32_t cand = 0u;
+        for (int k = 0; k < last; k++) {
+          float e;
+          const float v = closed_f(k, e);
+          if (!(v - e > umin)) cand |= 1u << k;
+        }
+        Val best{BIG, 0.f};
+        while (cand) {
+          const int k = __ffs(cand) - 1;
+          cand &= cand - 1u;
+          best = vmin(best, closed_df(k));
+        }
         R.sin = best.v;
         if (!certified(best)) R.flag = true;
       }
