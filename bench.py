@@ -35,6 +35,15 @@ import workloads as W  # noqa: E402
 
 N_QUERIES = 5
 BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 doubles out
+# DRAM bytes per track of each binary32 pass, from one ncu capture of the full-size step
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass); valid only while the kernel
+# sources hash to the value recorded with them, else the bench reports traffic = null.
+DRAM_CAPTURE = {
+    "sources_sha256": "1d3dc5780b85d7ae8c0e79b44183c11e04d6a035954787d4e38c477ec2190d6c",
+    "bytes_per_track": {'box': 79.04, 'trd': 78.95, 'tube': 79.3, 'cone': 79.46, 'polycone': 79.76},
+    "profile": "profiles/query_fp32_dram_full.md",
+}
+KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
 E2E_CHUNK = 1 << 21  # tracks per host-streaming chunk
 E2E_SLOTS = 3
 
@@ -159,6 +168,15 @@ def cpu_baseline_sweep(max_exp: int = 16):
     return {"cores": threads, "rows": res}
 
 
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1512_06637_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def gen_inputs(n: int):
     return {name: W.tracks_for_solid(spec, n, seed=2) for name, spec in specs()}
 
@@ -262,9 +280,15 @@ def run_ours(args):
     dom_ms = per_solid_ms[dom]
     peaks = load_peaks()
     achieved = n * BYTES_PER_TRACK / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    if precision == "fp32_refine" and kernel_sources_sha256() == DRAM_CAPTURE["sources_sha256"]:
+        per_track = DRAM_CAPTURE["bytes_per_track"].get(dom)
+        traffic = None if per_track is None else per_track * n
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": f"query pass ({precision}) on {dom}", "peak_source": peaks["source"]}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": f"query pass ({precision}) on {dom}", "peak_source": peaks["source"],
+                "traffic_source": DRAM_CAPTURE["profile"] if traffic is not None else
+                "none: the kernel sources changed since the last DRAM capture"}
 
     refined = None
     if ws is not None:
@@ -327,6 +351,7 @@ def run_e2e(gv, torch, inputs, solids, precision, n, steps, world):
     def step():
         for name in solids:
             gv.query_host(solids[name], host_in[name], host_out[name], pipe, precision=precision, stream=stream)
+        pipe.join(stream)
 
     step()
     torch.cuda.synchronize()
@@ -387,8 +412,8 @@ def bench_sweep(gv, torch):
     """The paper's measurement (its one figure): Box and Tube DistanceToOut throughput
     against the number of tracks N, for points inside with isotropic directions.  Per N
     the mean device time of one gv_query call over many repetitions (about 2^26 tracks
-    per N in total, at least 8 calls), and for N <= 2^16 one call replayed from a CUDA
-    graph as well."""
+    per N in total, at least 8 calls; for small N that is the host's submission rate),
+    and for N <= 2^16 one call replayed from a CUDA graph (the device's own rate)."""
     res = {}
     nmax = 1 << max(SWEEP_EXPONENTS)
     for name, spec in SWEEP_SPECS:
@@ -407,16 +432,18 @@ def bench_sweep(gv, torch):
                 ms = _timed(torch, lambda: gv.query(s, sub, precision=prec, out=out, workspace=ws), reps)
                 row[prec + "_tracks_per_s"] = n / (ms * 1e-3)
                 row[prec + "_us_per_call"] = ms * 1e3
-            if n <= 1 << 16:
-                stream = torch.cuda.Stream()
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.stream(stream):
-                    gv.query(s, sub, precision="fp32_refine", out=out, workspace=ws, stream=stream)
-                    torch.cuda.synchronize()
-                    with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
-                        gv.query(s, sub, precision="fp32_refine", out=out, workspace=ws, stream=stream)
-                ms = _timed(torch, g.replay, reps)
-                row["fp32_refine_graph_us_per_call"] = ms * 1e3
+            if n <= 1 << 16:  # small baskets: one captured call replayed (no host submission cost)
+                for prec in ("fp32_refine", "fp64"):
+                    stream = torch.cuda.Stream()
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.stream(stream):
+                        gv.query(s, sub, precision=prec, out=out, workspace=ws, stream=stream)
+                        torch.cuda.synchronize()
+                        with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                            gv.query(s, sub, precision=prec, out=out, workspace=ws, stream=stream)
+                    ms = _timed(torch, g.replay, reps)
+                    row[prec + "_graph_us_per_call"] = ms * 1e3
+                    row[prec + "_graph_tracks_per_s"] = n / (ms * 1e-3)
             rows.append(row)
         res[name] = rows
     return res

@@ -148,14 +148,16 @@ gv_status gv_pipeline_create(int64_t chunk_tracks, int32_t slots, gv_pipeline** 
 void gv_pipeline_destroy(gv_pipeline* p);
 /* Enqueues gv_query for host arrays (tracks->x..dz and res->* are HOST pointers,
  * 8-byte aligned, NULL result pointers skip that query).  The work starts after
- * everything enqueued on `stream` so far, and `stream` waits for its end: the
- * results are in the host arrays once `stream` has passed this point, and the
- * host arrays must stay valid and unchanged until then.  Consecutive calls on one
- * pipeline overlap (the last chunks of one with the first of the next).  A
- * pipeline must not be used from two threads at once.  Results are bit-identical
- * to gv_query on the same tracks. */
+ * everything enqueued on `stream` so far; `stream` itself does not wait for it.
+ * Consecutive calls on one pipeline overlap (the last chunks of one with the first
+ * of the next).  A pipeline must not be used from two threads at once.  Results
+ * are bit-identical to gv_query on the same tracks. */
 gv_status gv_query_host(const gv_solid* s, const gv_tracks* host_tracks, gv_precision prec,
                         const gv_results* host_results, gv_pipeline* p, void* stream);
+/* Makes `stream` wait for every gv_query_host call made on the pipeline so far: their
+ * results are in the host arrays once `stream` has passed this point, and their host
+ * arrays must stay valid and unchanged until then. */
+gv_status gv_pipeline_join(gv_pipeline* p, void* stream);
 
 /* --- mixed baskets in one launch --------------------------------------------
  * The scheduler of the paper (Project goals, item 1) collects particles that sit

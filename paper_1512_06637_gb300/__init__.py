@@ -147,6 +147,10 @@ class Pipeline:
         check(lib().gv_pipeline_create(int(chunk_tracks), int(slots), ctypes.byref(h)))
         self.handle = h
 
+    def join(self, stream=None):
+        """``stream`` waits for every query_host call made on this pipeline so far."""
+        check(lib().gv_pipeline_join(self.handle, _stream_ptr(stream)))
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value and _abi._lib is not None:
@@ -172,8 +176,9 @@ def _host_ptr(a, dtype, n, name):
 
 def query_host(solid: Solid, tracks: dict, out: dict, pipeline: Pipeline, precision: str = "fp64",
                stream=None) -> dict:
-    """gv_query for host arrays (numpy or CPU tensors, pinned for full speed): enqueued on
-    ``stream``; the results are in ``out`` once that stream has passed this call."""
+    """gv_query for host arrays (numpy or CPU tensors, pinned for full speed): starts after
+    the work on ``stream``; the results are in ``out`` once ``stream`` has passed a later
+    ``pipeline.join(stream)``."""
     import numpy as np
     n = int(tracks["x"].size if isinstance(tracks["x"], np.ndarray) else tracks["x"].numel())
     t = _abi.Tracks(*(_host_ptr(tracks.get(k), np.float64, n, k) for k in ("x", "y", "z", "dx", "dy", "dz")), n)

@@ -67,6 +67,7 @@ SIGNATURES = {
     "gv_query": (_i, [_p, ctypes.POINTER(Tracks), _i, ctypes.POINTER(Results), _p, _p]),
     "gv_pipeline_create": (_i, [_i64, ctypes.c_int32, _p]),
     "gv_pipeline_destroy": (None, [_p]),
+    "gv_pipeline_join": (_i, [_p, _p]),
     "gv_query_host": (_i, [_p, ctypes.POINTER(Tracks), _i, ctypes.POINTER(Results), _p, _p]),
     "gv_batch_create": (_i, [_p, ctypes.c_int32, _p, ctypes.c_int32, _p]),
     "gv_batch_set_config": (_i, [_p, ctypes.POINTER(BatchConfig)]),

@@ -6,7 +6,9 @@
 // the slot's previous chunk was evaluated (the inputs are free), its evaluation
 // waits for its input copy and for the slot's previous output copy (the outputs
 // are free), its output copy waits for its evaluation.  Events carry every
-// dependency; nothing synchronises the host.
+// dependency; nothing synchronises the host.  A call waits for the caller's stream as it
+// was when the call was made; the caller's stream waits for the pipeline only at
+// gv_pipeline_join, so consecutive calls keep the copy engines busy across baskets.
 #include <new>
 #include "gv_internal.h"
 
@@ -165,9 +167,15 @@ gv_status gv_query_host(const gv_solid* s, const gv_tracks* t, gv_precision prec
     if (e == cudaSuccess) e = cudaEventRecord(S.out_done, p->s_out);
     S.used = true;
   }
-  // the caller's stream continues after the last copy out (the out stream is in order)
-  if (e == cudaSuccess) e = cudaEventRecord(p->fin, p->s_out);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, p->fin, 0);
   if (e != cudaSuccess) return cuda_error(e, "gv_query_host");
+  return GV_OK;
+}
+
+gv_status gv_pipeline_join(gv_pipeline* p, void* stream) {
+  if (!p) return set_error(GV_ERR_INVALID_ARG, "NULL pipeline");
+  // the out stream is in order: its last copy is the end of every call made so far
+  cudaError_t e = cudaEventRecord(p->fin, p->s_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, p->fin, 0);
+  if (e != cudaSuccess) return cuda_error(e, "gv_pipeline_join");
   return GV_OK;
 }

@@ -35,24 +35,8 @@ __global__ void __launch_bounds__(256, FAMILY == 0 ? 4 : (FAMILY == 1 ? 2 : 3)) 
               *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
   const unsigned lane = threadIdx.x & 31u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // Polycones of several sections: inside and outside tracks take different paths (one
-  // section and the exit search, against every section and the entry search), so each block first sorts
-  // its chunk of tracks by a binary32 estimate of the side and hands inside tracks to the
-  // first warps and outside tracks to the last; results do not depend on the estimate.
-  __shared__ uint16_t perm[256];
-  __shared__ int n_side[2];
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
-    int64_t i = base + threadIdx.x;
-    if (FAMILY == 3 && S.nz > 2) {
-      if (threadIdx.x < 2) n_side[threadIdx.x] = 0;
-      __syncthreads();
-      const bool in_est = i < a.n && f32::inside_estimate(S, X, Y, Z, i);
-      const int at = in_est ? atomicAdd(&n_side[0], 1) : (int)blockDim.x - 1 - atomicAdd(&n_side[1], 1);
-      perm[at] = (uint16_t)threadIdx.x;
-      __syncthreads();
-      i = base + perm[threadIdx.x];
-      __syncthreads();
-    }
+    const int64_t i = base + threadIdx.x;
     const bool valid = i < a.n;
     bool flag = false;
     if (valid) {
@@ -87,6 +71,93 @@ __global__ void __launch_bounds__(256, FAMILY == 0 ? 4 : (FAMILY == 1 ? 2 : 3)) 
   }
 }
 
+// Results of one finished track: written when certified, else its index appended to
+// the worklist of the binary64 pass.
+__device__ __forceinline__ void finish_track(const QueryArgs& a, int64_t i, const f32::R32& R, uint32_t* worklist,
+                                             unsigned long long* counter) {
+  if (R.flag) {
+    worklist[atomicAdd(counter, 1ull)] = (uint32_t)i;
+    return;
+  }
+  if (a.inside) a.inside[i] = (int8_t)R.code;
+  if (a.din) reinterpret_cast<unsigned long long*>(a.din)[i] = f32::f2d_bits(R.din);
+  if (a.dout) reinterpret_cast<unsigned long long*>(a.dout)[i] = f32::f2d_bits(R.dout);
+  if (a.sin) reinterpret_cast<unsigned long long*>(a.sin)[i] = f32::f2d_bits(R.sin);
+  if (a.sout) reinterpret_cast<unsigned long long*>(a.sout)[i] = f32::f2d_bits(R.sout);
+}
+
+// Tube / cone / polycone with lane refill.  A track's distance walk visits one to several
+// sections, and lanes of a warp finish at different times.  Each warp keeps one track
+// per lane in registers (its point, direction and walk state) and loops: when at least
+// half its lanes are idle, the idle lanes take the next tracks from a dispenser counter
+// (one atomicAdd per warp) and run the setup (code, safeties, first section); then every
+// busy lane advances its walk by one section; a lane whose walk ends writes its results
+// and becomes idle.  Warps stay mostly full until the dispenser runs dry.
+constexpr int kRefillIdle = 16;
+// tube and one-section cones: the walk is one or two sections long, so the plain kernel
+// (one track per thread, no refill) is used for them
+constexpr bool kWalkOneSection = false;
+
+template <int FAMILY>
+__global__ void __launch_bounds__(256, 2) k_query_walk(const Desc* __restrict__ desc, QueryArgs a,
+                                                      uint32_t* __restrict__ worklist,
+                                                      unsigned long long* __restrict__ counter) {
+  __shared__ Desc S;
+  stage_desc32(S, desc);
+  __syncthreads();
+  const unsigned want = (a.inside ? f32::kWantCode : 0u) | (a.din ? f32::kWantDin : 0u) |
+                        (a.dout ? f32::kWantDout : 0u) | (a.sin ? f32::kWantSin : 0u) |
+                        (a.sout ? f32::kWantSout : 0u);
+  const bool dirs = want & (f32::kWantDin | f32::kWantDout);
+  const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
+              *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
+              *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
+  constexpr bool TUBE = FAMILY == 2;
+  unsigned long long* dispenser = counter + 1;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
+  bool busy = false, more = true;
+  int64_t i = 0;
+  f32::TrackF T;
+  f32::R32 R;
+  f32::Walk W;
+  while (true) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !busy);
+    if (more && (__popc(idle) >= kRefillIdle || idle == 0xffffffffu)) {
+      unsigned long long first = 0;
+      if (lane == 0) first = atomicAdd(dispenser, (unsigned long long)__popc(idle));
+      first = __shfl_sync(0xffffffffu, first, 0);
+      if (first + __popc(idle) >= (unsigned long long)a.n) more = false;
+      if (!busy) {
+        const unsigned long long j = first + __popc(idle & below);
+        if (j < (unsigned long long)a.n) {
+          i = (int64_t)j;
+          T = f32::load_track<true>(X, Y, Z, Ux, Uy, Uz, i, dirs);
+          R.flag = T.bad;
+          R.code = 1;
+          R.din = R.dout = R.sin = R.sout = 0.f;
+          W.need_in = W.need_out = false;
+          W.live = false;
+          if (!R.flag) busy = f32::pcon_begin<TUBE>(S, T, want, R, W);
+          if (!busy) finish_track(a, i, R, worklist, counter);
+        }
+      }
+    }
+    if (__ballot_sync(0xffffffffu, busy) == 0u) {
+      if (!more) break;
+      continue;
+    }
+    if (busy) {
+      f32::pcon_step<TUBE>(S, T, W);
+      if (!W.live) {
+        f32::pcon_end(W, R);
+        finish_track(a, i, R, worklist, counter);
+        busy = false;
+      }
+    }
+  }
+}
+
 template <int FAMILY>
 __global__ void __launch_bounds__(256) k_refine_fp64(const Desc* __restrict__ desc, QueryArgs a,
                                                      const uint32_t* __restrict__ worklist,
@@ -117,14 +188,18 @@ __global__ void __launch_bounds__(256) k_refine_fp64(const Desc* __restrict__ de
 
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,
                               unsigned long long* counter, cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
+  // counter[0]: worklist length; counter[1]: next track of the lane-refill dispenser
+  cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess || a.n == 0) return e;
   const int threads = 256;
   int64_t blocks = (a.n + threads - 1) / threads;
   const int sms = sm_count();
   const int64_t cap = (int64_t)sms * 8;
   if (blocks > cap) blocks = cap;
-  const unsigned rblocks = (unsigned)sms * 2;
+  // lane-refill kernel: resident blocks only (two per SM), fed by the dispenser
+  const unsigned wblocks = (unsigned)(blocks < (int64_t)sms * 2 ? blocks : (int64_t)sms * 2);
+  // the worklist holds at most n tracks: no more refinement blocks than that needs
+  const unsigned rblocks = (unsigned)(blocks < (int64_t)sms * 2 ? blocks : (int64_t)sms * 2);
   switch (s->h.type) {
     case kBox:
       k_query_fp32<0><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
@@ -136,11 +211,17 @@ cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* w
       k_refine_fp64<1><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
     case kTube:
-      k_query_fp32<2><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+      if (kWalkOneSection)
+        k_query_walk<2><<<wblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+      else
+        k_query_fp32<2><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       k_refine_fp64<2><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
     default:
-      k_query_fp32<3><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+      if (s->h.nz > 2 || kWalkOneSection)
+        k_query_walk<3><<<wblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+      else
+        k_query_fp32<3><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       k_refine_fp64<2><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
   }

@@ -620,28 +620,21 @@ __device__ __forceinline__ bool lt_sure(Val a, Val b, bool& unsure) {
   return a.v < b.v;
 }
 
-// Binary32 estimate of "inside" for a polycone-family solid from the hi parts only (used
-// to group tracks; no result depends on it).
-__device__ __forceinline__ bool inside_estimate(const Desc& S, const uint2* x, const uint2* y, const uint2* z,
-                                                int64_t i) {
-  bool bad = false;
-  const float px = trunc_hi(__ldg(x + i), bad), py = trunc_hi(__ldg(y + i), bad), pz = trunc_hi(__ldg(z + i), bad);
-  const int nz = S.nz;
-  if (!(pz > S.zh[0] && pz < S.zh[nz - 1])) return false;
-  int k = 0;
-  while (k < nz - 2 && pz >= S.zh[k + 1]) k++;
-  const float r = sqrtf(px * px + py * py);
-  if (r > fmaf(S.oah[k], pz, S.obh[k])) return false;
-  if (((S.inner >> k) & 1u) && r < fmaf(S.iah[k], pz, S.ibh[k])) return false;
-  if (S.flags & kHasPhi) {
-    const float a = S.nsh[0] * px + S.nsh[1] * py, b = S.neh[0] * px + S.neh[1] * py;
-    if (((S.flags & kPhiWide) ? fminf(a, b) : fmaxf(a, b)) > 0.f) return false;
-  }
-  return true;
-}
+// The state of one track's distance walk between two sections (see pcon_begin).
+enum : int { kSearch = 0, kStretch = 1, kDone = 2 };
+struct Walk {
+  F2 rad, A0;        // p.d_xy and u^2 + v^2, double-float
+  Iv PH, X2;         // narrow-phi interval, wide-phi excluded wedge
+  Val tcur, ans;     // search/stretch position, answer
+  float rh, rl, r2h, erad, iw;
+  int k, step, st, guard;
+  bool zc, answered, u, goal_out, surf, need_in, need_out, in_range, live;
+};
 
 template <bool TUBE, bool FRAME = false>
-__device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32& R) {
+__device__ inline bool pcon_begin(const Desc& S, const TrackF& T, unsigned want, R32& R, Walk& W) {
+  W.live = false;
+  W.need_in = W.need_out = false;
   const int nz = S.nz, last = nz - 1;
   // r = sqrt(x^2 + y^2) in double-float
   const F2 x2 = tprod(T.xh, T.xh), y2 = tprod(T.yh, T.yh);
@@ -766,7 +759,7 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
       }
     }
   }
-  if (!(want & (kWantDin | kWantDout))) return;
+  if (!(want & (kWantDin | kWantDout))) return false;
 
   const F2 rad = radial_df(T);
   const float radial = rad.h;
@@ -827,9 +820,9 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
   }
   if (R.code == 0 && (want & kWantDin)) R.din = -1.f;
   if (R.code == 2 && (want & kWantDout)) R.dout = -1.f;
-  const bool need_out = (R.code == 0 || entering) && (want & kWantDout);
-  const bool need_in = (R.code == 2 || leaving) && (want & kWantDin);
-  if (!need_out && !need_in) return;
+  W.need_out = (R.code == 0 || entering) && (want & kWantDout);
+  W.need_in = (R.code == 2 || leaving) && (want & kWantDin);
+  if (!W.need_out && !W.need_in) return false;
 
   // Distances in interval form, over the sections the ray meets for t >= 0 in t order.
   // In section k the ray is inside the solid on C \ (X1 u X2): C = outer region of the
@@ -852,158 +845,206 @@ __device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32
     else X2 = iv_and(iv_half(pa.g, pa.E, nds, ends, false, u), iv_half(pb.g, pb.E, nde, ende, false, u));
     if (!X2.empty && !(X2.lo.v < X2.hi.v)) X2 = iv_none();
   }
-  const float iw = T.w != 0 ? __frcp_rn(T.w) : 0.f;
-  auto plane_t = [&](int j) -> Val {
-    const float num = (S.zh[j] - T.zh) + (S.zl[j] - T.zl);
-    const float t = num * iw;
-    float e = fmaf(G42, fabsf(T.zh) + fabsf(S.zh[j]), T.fl);
-    if (FRAME) e = fmaf(1.01f * fabsf(t), T.dfl, e);
-    return {t, fmaf(5.f * U, fabsf(t), e * fabsf(iw))};
-  };
-  int k, step;
-  bool in_range = true;  // for w == 0: the ray's z inside [z0, zN]
+  W.iw = T.w != 0 ? __frcp_rn(T.w) : 0.f;
+  W.rad = rad;
+  W.A0 = A0;
+  W.erad = erad;
+  W.rh = rh;
+  W.rl = rl;
+  W.r2h = r2h;
+  W.PH = PH;
+  W.X2 = X2;
+  W.in_range = true;  // for w == 0: the ray's z inside [z0, zN]
   if (FRAME && fabsf(T.w) <= 4.f * T.dfl) u = true;  // the order of the sections is not certain
   // below z0 (above zN) the first section is k0 = 0 (k0 = nz - 2) already
-  if (T.w > 0) { step = 1; k = k0; }
-  else if (T.w < 0) { step = -1; k = k0; }
-  else {  // the ray stays in the plane z = const: one section or none
-    step = 0; k = k0;
-    in_range = !(gz0 > 0) && !(gz1 > 0);
+  W.k = k0;
+  if (T.w > 0) {
+    W.step = 1;
+  } else if (T.w < 0) {
+    W.step = -1;
+  } else {  // the ray stays in the plane z = const: one section or none
+    W.step = 0;
+    W.in_range = !(gz0 > 0) && !(gz1 > 0);
     for (int j = k0; j <= k0 + 1; j++) {  // on a plane the pieces on both sides meet: binary64
       const float gj = (S.zh[j] - T.zh) + (S.zl[j] - T.zl);
       if (fabsf(gj) <= 4.f * U * fabsf(gj) + G42 * (fabsf(T.zh) + fabsf(S.zh[j])) + T.fl) u = true;
     }
   }
+  W.goal_out = W.need_out;
+  W.surf = surf;
+  W.st = R.code == 0 ? kStretch : kSearch;
+  W.tcur = Val{0.f, 0.f};
+  W.zc = surf;  // tcur is 0+
+  W.ans = Val{BIG, 0.f};
+  W.answered = false;
+  W.u = u;
+  W.guard = 0;
+  W.live = true;
+  return true;
+}
+
+// The binary32 time of z-plane j along the track, with its bound.
+template <bool FRAME>
+__device__ __forceinline__ Val plane_time(const Desc& S, const TrackF& T, float iw, int j) {
+  const float num = (S.zh[j] - T.zh) + (S.zl[j] - T.zl);
+  const float t = num * iw;
+  float e = fmaf(G42, fabsf(T.zh) + fabsf(S.zh[j]), T.fl);
+  if (FRAME) e = fmaf(1.01f * fabsf(t), T.dfl, e);
+  return {t, fmaf(5.f * U, fabsf(t), e * fabsf(iw))};
+}
+
+// One section of the walk: the section W.k and its intervals, SEARCH and STRETCH in it,
+// then the next section.  W.live turns false when the walk is over.
+template <bool TUBE, bool FRAME = false>
+__device__ inline void pcon_step(const Desc& S, const TrackF& T, Walk& W) {
+  const int last = S.nz - 1;
+  const int k0 = W.k;  // (unused name kept short below)
+  (void)k0;
+  bool u = W.u;
   // An outside track looks only for an entry: while searching it passes over the sections
   // whose slab the ray crosses (t >= 0) farther from the axis than the section's largest
   // outer radius, by a wide margin; a section not certainly missed is examined in full.
   auto may_enter = [&](int j) -> bool {
-    const float t0 = plane_t(j).v, t1 = plane_t(j + 1).v;
+    const float t0 = plane_time<FRAME>(S, T, W.iw, j).v, t1 = plane_time<FRAME>(S, T, W.iw, j + 1).v;
     const float m = fmaf(1e-5f, fabsf(t0) + fabsf(t1), 1e-6f);
     const float lo = fmaxf(fminf(t0, t1) - m, 0.f), hi = fmaxf(t0, t1) + m;
     if (hi < lo) return false;  // behind the start
-    const float tm = fminf(fmaxf(A0.h > 0.f ? -radial / A0.h : lo, lo), hi);
-    const float r2 = fmaf(fmaf(A0.h, tm, 2.f * radial), tm, r2h);
+    const float radial = W.rad.h;
+    const float tm = fminf(fmaxf(W.A0.h > 0.f ? -radial / W.A0.h : lo, lo), hi);
+    const float r2 = fmaf(fmaf(W.A0.h, tm, 2.f * radial), tm, W.r2h);
     const float Rm = fmaxf(fmaf(S.oah[j], S.zh[j], S.obh[j]), fmaf(S.oah[j], S.zh[j + 1], S.obh[j]));
-    const float mag = r2h + 2.f * fabsf(radial * tm) + A0.h * tm * tm + Rm * Rm;
+    const float mag = W.r2h + 2.f * fabsf(radial * tm) + W.A0.h * tm * tm + Rm * Rm;
     return !(r2 - Rm * Rm > fmaf(1e-5f, mag, 1e-6f));
   };
-  enum { kSearch, kStretch, kDone };
-  const bool goal_out = need_out;
-  int st = R.code == 0 ? kStretch : kSearch;
-  Val tcur{0.f, 0.f};
-  bool zc = surf;   // tcur is 0+
-  Val ans{BIG, 0.f};
-  bool answered = false;
-  for (int guard = 0; guard < kMaxZ && st != kDone; guard++) {
-    if (step != 0 && st == kSearch && S.nz > 2) {
-      while (k >= 0 && k <= last - 1 && !may_enter(k)) k += step;
-      if (k < 0 || k > last - 1) break;
+  int k = W.k;
+  const int step = W.step;
+  if (step != 0 && W.st == kSearch && S.nz > 2) {
+    while (k >= 0 && k <= last - 1 && !may_enter(k)) k += step;
+    if (k < 0 || k > last - 1) {
+      W.k = k;
+      W.live = false;
+      return;
     }
-    Iv slab = iv_all();
-    if (step != 0) {
-      const Val ta = plane_t(k), tb = plane_t(k + 1);
-      slab = step > 0 ? Iv{ta, tb, false} : Iv{tb, ta, false};
-    } else if (!in_range) {
-      slab = iv_none();
-    }
-    const bool beyond = !slab.empty && slab.hi.v < -slab.hi.e;  // this section is behind the ray
-    if (!beyond) {
-      const float ao = TUBE ? 0.f : S.oah[k];
-      const Lat Lo = k == k0 ? lo_ : lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], rh, rl, T, true);
-      const Quad qo = quad32<TUBE, FRAME>(ao, TUBE ? 0.f : S.oal[k], Lo, T, rad, erad, A0, rh, rl);
-      u |= qo.unsure;
-      const Iv lat = iv_and(iv_region(qo, Lo.g, Lo.E, u), PH);  // lateral and phi part of C
-      Iv X1 = iv_none();
-      if ((S.inner >> k) & 1u) {
-        const float ai = TUBE ? 0.f : S.iah[k];
-        const Lat Li = k == k0 ? li_ : lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], rh, rl, T, false);
-        const Quad qi = quad32<TUBE, FRAME>(ai, TUBE ? 0.f : S.ial[k], Li, T, rad, erad, A0, rh, rl);
-        u |= qi.unsure;
-        X1 = iv_region(qi, -Li.g, Li.E, u);
-        if (!X1.empty && !(X1.lo.v < X1.hi.v)) X1 = iv_none();
-      }
-      const Iv C = iv_and(lat, slab);
-      // v at or before tcur (passed): the same crossing, certainly earlier, or within 0+
-      auto passed = [&](Val v) -> bool {
-        if (zc) return !after0(v);
-        if (v.v == tcur.v) return true;
-        return !lt_sure(tcur, v, u);
-      };
-      // SEARCH: the first point of C \ (X1 u X2) after tcur in this section
-      auto search = [&]() {
-        if (C.empty || passed(C.hi)) return;
-        Val t = tcur;
-        bool z = zc;
-        if (!passed(C.lo)) { t = C.lo; z = false; }
-        for (int pass = 0; pass < 2; pass++) {
-          const Iv* X[2] = {&X1, &X2};
-          for (int j = 0; j < 2; j++) {
-            if (X[j]->empty || (!z && t.v == X[j]->hi.v)) continue;
-            const bool lo_passed = z ? !after0(X[j]->lo) : (X[j]->lo.v == t.v || !lt_sure(t, X[j]->lo, u));
-            const bool hi_ahead = z ? after0(X[j]->hi) : lt_sure(t, X[j]->hi, u);
-            if (lo_passed && hi_ahead) { t = X[j]->hi; z = false; }
-          }
-        }
-        if (!z && (t.v == C.hi.v || !lt_sure(t, C.hi, u))) return;  // pushed past C
-        if (!goal_out && !z) {  // an entry: the answer
-          if (!surf && !(t.v > t.e)) u = true;  // an outside point enters strictly after 0
-          ans = t;
-          answered = true;
-          st = kDone;
-          return;
-        }
-        st = kStretch;  // DistanceToOut from the piece's start, or a leaving point inside at 0+
-        tcur = t;
-        zc = z;
-      };
-      if (st == kSearch) search();
-      if (st == kStretch) {
-        const int at = in_piece(lat, X1, X2, tcur, zc);
-        Val e = lat.hi;  // end of the inside stretch holding tcur
-        if (!X1.empty && (zc ? after0(X1.lo) : X1.lo.v > tcur.v)) e = vmin(e, X1.lo);
-        if (!X2.empty && (zc ? after0(X2.lo) : X2.lo.v > tcur.v)) e = vmin(e, X2.lo);
-        if (at <= 0) {  // the section must hold tcur (the profile is continuous)
-          u = true;
-          st = kDone;
-        } else if (step != 0 && lt_sure(slab.hi, e, u)) {  // reaches the far plane first
-          const bool end_plane = (step > 0 && k + 1 == last) || (step < 0 && k == 0);
-          if (!end_plane) {
-            tcur = slab.hi;
-            zc = false;
-          } else if (goal_out) {
-            ans = slab.hi;
-            answered = true;
-            st = kDone;
-          } else {
-            st = kDone;  // leaves through an end plane: no entry after it
-          }
-        } else if (goal_out) {
-          ans = e;
-          answered = true;
-          st = kDone;
-        } else {  // a leaving point's stretch ends: look for the next entry
-          tcur = e;
-          zc = false;
-          st = kSearch;
-          search();
-        }
-      }
-    }
-    k += step;
-    if (step == 0 || k < 0 || k > last - 1) break;
   }
-  if (st == kStretch) u = true;  // a stretch must end at a surface
-  if (need_out) {
+  Iv slab = iv_all();
+  if (step != 0) {
+    const Val ta = plane_time<FRAME>(S, T, W.iw, k), tb = plane_time<FRAME>(S, T, W.iw, k + 1);
+    slab = step > 0 ? Iv{ta, tb, false} : Iv{tb, ta, false};
+  } else if (!W.in_range) {
+    slab = iv_none();
+  }
+  const bool beyond = !slab.empty && slab.hi.v < -slab.hi.e;  // this section is behind the ray
+  if (!beyond) {
+    const float ao = TUBE ? 0.f : S.oah[k];
+    const Lat Lo = lateral<TUBE>(S.oah[k], S.oal[k], S.obh[k], S.obl[k], S.ok_[k], W.rh, W.rl, T, true);
+    const Quad qo = quad32<TUBE, FRAME>(ao, TUBE ? 0.f : S.oal[k], Lo, T, W.rad, W.erad, W.A0, W.rh, W.rl);
+    u |= qo.unsure;
+    const Iv lat = iv_and(iv_region(qo, Lo.g, Lo.E, u), W.PH);  // lateral and phi part of C
+    Iv X1 = iv_none();
+    if ((S.inner >> k) & 1u) {
+      const float ai = TUBE ? 0.f : S.iah[k];
+      const Lat Li = lateral<TUBE>(S.iah[k], S.ial[k], S.ibh[k], S.ibl[k], S.ik_[k], W.rh, W.rl, T, false);
+      const Quad qi = quad32<TUBE, FRAME>(ai, TUBE ? 0.f : S.ial[k], Li, T, W.rad, W.erad, W.A0, W.rh, W.rl);
+      u |= qi.unsure;
+      X1 = iv_region(qi, -Li.g, Li.E, u);
+      if (!X1.empty && !(X1.lo.v < X1.hi.v)) X1 = iv_none();
+    }
+    const Iv& X2 = W.X2;
+    const Iv C = iv_and(lat, slab);
+    // v at or before tcur (passed): the same crossing, certainly earlier, or within 0+
+    auto passed = [&](Val v) -> bool {
+      if (W.zc) return !after0(v);
+      if (v.v == W.tcur.v) return true;
+      return !lt_sure(W.tcur, v, u);
+    };
+    // SEARCH: the first point of C \ (X1 u X2) after tcur in this section
+    auto search = [&]() {
+      if (C.empty || passed(C.hi)) return;
+      Val t = W.tcur;
+      bool z = W.zc;
+      if (!passed(C.lo)) { t = C.lo; z = false; }
+      for (int pass = 0; pass < 2; pass++) {
+        const Iv* X[2] = {&X1, &X2};
+        for (int j = 0; j < 2; j++) {
+          if (X[j]->empty || (!z && t.v == X[j]->hi.v)) continue;
+          const bool lo_passed = z ? !after0(X[j]->lo) : (X[j]->lo.v == t.v || !lt_sure(t, X[j]->lo, u));
+          const bool hi_ahead = z ? after0(X[j]->hi) : lt_sure(t, X[j]->hi, u);
+          if (lo_passed && hi_ahead) { t = X[j]->hi; z = false; }
+        }
+      }
+      if (!z && (t.v == C.hi.v || !lt_sure(t, C.hi, u))) return;  // pushed past C
+      if (!W.goal_out && !z) {  // an entry: the answer
+        if (!W.surf && !(t.v > t.e)) u = true;  // an outside point enters strictly after 0
+        W.ans = t;
+        W.answered = true;
+        W.st = kDone;
+        return;
+      }
+      W.st = kStretch;  // DistanceToOut from the piece's start, or a leaving point inside at 0+
+      W.tcur = t;
+      W.zc = z;
+    };
+    if (W.st == kSearch) search();
+    if (W.st == kStretch) {
+      const int at = in_piece(lat, X1, X2, W.tcur, W.zc);
+      Val e = lat.hi;  // end of the inside stretch holding tcur
+      if (!X1.empty && (W.zc ? after0(X1.lo) : X1.lo.v > W.tcur.v)) e = vmin(e, X1.lo);
+      if (!X2.empty && (W.zc ? after0(X2.lo) : X2.lo.v > W.tcur.v)) e = vmin(e, X2.lo);
+      if (at <= 0) {  // the section must hold tcur (the profile is continuous)
+        u = true;
+        W.st = kDone;
+      } else if (step != 0 && lt_sure(slab.hi, e, u)) {  // reaches the far plane first
+        const bool end_plane = (step > 0 && k + 1 == last) || (step < 0 && k == 0);
+        if (!end_plane) {
+          W.tcur = slab.hi;
+          W.zc = false;
+        } else if (W.goal_out) {
+          W.ans = slab.hi;
+          W.answered = true;
+          W.st = kDone;
+        } else {
+          W.st = kDone;  // leaves through an end plane: no entry after it
+        }
+      } else if (W.goal_out) {
+        W.ans = e;
+        W.answered = true;
+        W.st = kDone;
+      } else {  // a leaving point's stretch ends: look for the next entry
+        W.tcur = e;
+        W.zc = false;
+        W.st = kSearch;
+        search();
+      }
+    }
+  }
+  W.u = u;
+  W.k = k + step;
+  W.guard++;
+  if (W.st == kDone || step == 0 || W.k < 0 || W.k > last - 1 || W.guard >= kMaxZ) W.live = false;
+}
+
+// The distances from a finished walk (nothing when none was needed).
+__device__ inline void pcon_end(const Walk& W, R32& R) {
+  bool u = W.u;
+  if (W.st == kStretch) u = true;  // a stretch must end at a surface
+  if (W.need_out) {
     // entering surface point whose ray never gets inside: 0
-    const Val d = answered ? ans : Val{0.f, 0.f};
+    const Val d = W.answered ? W.ans : Val{0.f, 0.f};
     if (u || !certified(d)) R.flag = true;
     R.dout = unbig(d.v);
   }
-  if (need_in) {
-    if (u || !certified(ans)) R.flag = true;
-    R.din = answered ? ans.v : F_INF;
+  if (W.need_in) {
+    if (u || !certified(W.ans)) R.flag = true;
+    R.din = W.answered ? W.ans.v : F_INF;
   }
+}
+
+template <bool TUBE, bool FRAME = false>
+__device__ inline void pcon32(const Desc& S, const TrackF& T, unsigned want, R32& R) {
+  Walk W;
+  if (pcon_begin<TUBE, FRAME>(S, T, want, R, W))
+    while (W.live) pcon_step<TUBE, FRAME>(S, T, W);
+  pcon_end(W, R);
 }
 
 }  // namespace f32

@@ -54,6 +54,7 @@ def test_host_equals_device(gv, name, precision):
         host_in = {k: torch.from_numpy(v).pin_memory() for k, v in tr.items()} if pinned else tr
         out = host_out(n, pinned)
         gv.query_host(s, host_in, out, p, precision=precision)
+        p.join()
         torch.cuda.synchronize()
         for k in QUERIES:
             assert np.array_equal(as_np(out[k]), ref[k].cpu().numpy(), equal_nan=True), (pinned, k)
@@ -72,6 +73,7 @@ def test_host_partial_small_and_overlapping(gv):
     out = host_out(777, True, ("inside", "safety_in", "safety_out"))
     s = gv.Solid.from_spec(spec)
     gv.query_host(s, pts, out, p, precision="fp64")
+    p.join()
     torch.cuda.synchronize()
     want = oracle.Solid.from_spec(spec).query(**tr)
     compare({k: as_np(v) for k, v in out.items()}, want, "fp64", "host-partial")
@@ -89,6 +91,7 @@ def test_host_partial_small_and_overlapping(gv):
                       precision="fp32_refine")
         outs.append(o)
         trs.append(t)
+    p.join()
     torch.cuda.synchronize()
     for sp, t, o in zip(specs, trs, outs):
         compare({k: as_np(v) for k, v in o.items()}, oracle.Solid.from_spec(sp).query(**t), "fp32", "host-seq")
