@@ -39,8 +39,8 @@ BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 double
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass); valid only while the kernel
 # sources hash to the value recorded with them, else the bench reports traffic = null.
 DRAM_CAPTURE = {
-    "sources_sha256": "1d3dc5780b85d7ae8c0e79b44183c11e04d6a035954787d4e38c477ec2190d6c",
-    "bytes_per_track": {'box': 79.04, 'trd': 78.95, 'tube': 79.3, 'cone': 79.46, 'polycone': 79.76},
+    "sources_sha256": "f1833b9c497fc5b2e196a50b257ab691fbc3a818904010f04a4d680e5898e0e1",
+    "bytes_per_track": {'box': 79.05, 'trd': 78.96, 'tube': 79.26, 'cone': 79.42, 'polycone': 79.77},
     "profile": "profiles/query_fp32_dram_full.md",
 }
 KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
@@ -326,6 +326,7 @@ def run_ours(args):
         line["sweep_dist_out"] = bench_sweep(gv, torch)
         line["batched"] = bench_batched(gv, torch, max(3, args.steps), peaks)
         line["nav"] = bench_nav(gv, torch, max(3, args.steps))
+        line["transport"] = bench_transport(gv, torch)
         if rank == 0:
             line["serving"] = bench_serving(gv, torch)
     if rank == 0 and not args.no_cpu:
@@ -355,17 +356,23 @@ def run_e2e(gv, torch, inputs, solids, precision, n, steps, world):
 
     step()
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
-        step()
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = reduce_max(a.elapsed_time(b), world)
+    # The host link is shared with the machine's other GPUs and their jobs: time three
+    # separate windows and report the median one (all three are listed).
+    windows = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        windows.append(reduce_max(a.elapsed_time(b), world))
+    ms = sorted(windows)[1]
     h2d = sum(t.numel() * t.element_size() for tr in host_in.values() for t in tr.values())
     d2h = sum(t.numel() * t.element_size() for tr in host_out.values() for t in tr.values())
     return {"value": aggregate(steps * len(solids) * n * N_QUERIES, world, ms), "unit": "queries/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "windows_ms_per_step": [w / steps for w in windows], "statistic": "median of 3 windows",
             "path": f"gv_query_host, chunks of {E2E_CHUNK} tracks, {E2E_SLOTS} staging slots"}
 
 
@@ -486,6 +493,26 @@ def bench_fp64_m2(gv, torch, peaks, reps=20):
         res[name] = {"queries_per_s": n * N_QUERIES / (ms * 1e-3), "us": ms * 1e3, "hbm_gbs": gbs,
                      "hbm_frac": gbs / peaks["hbm_gbs"]}
     return res
+
+
+def bench_transport(gv, torch, reps=3, n=1 << 20, kmax=64):
+    """The transport loop (binary64): 2^20 tracks uniform in the nested detector, vacuum world,
+    light shells and dense cells, random numbers given; tracks and steps per second."""
+    geo = W.nested_geometry()
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    tr = W.nested_tracks(n, seed=11, geom=geo)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in tr.items()}
+    node0 = G.locate(dev)
+    m = W.transport_materials(geo)
+    mat = torch.from_numpy(m["node_material"]).cuda()
+    sig = torch.from_numpy(m["sigma_n"]).cuda()
+    xi = torch.from_numpy(W.transport_xi(n, kmax, seed=1)).cuda()
+    out = G.transport(dev, node0, mat, sig, xi, kmax)
+    ms = _timed(torch, lambda: G.transport(dev, node0, mat, sig, xi, kmax, out=out), reps)
+    steps = int(out["steps"].sum().item())
+    return {"workload": "nested detector, 2^20 tracks, kmax 64, binary64", "tracks_per_s": n / (ms * 1e-3),
+            "steps_per_s": steps / (ms * 1e-3), "mean_steps": steps / n, "ms": ms,
+            "reasons": torch.bincount(out["reason"].long(), minlength=4).tolist()}
 
 
 def bench_batched(gv, torch, reps, peaks):

@@ -233,6 +233,40 @@ gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* tracks, int32_t* node
 gv_status gv_nav_step(const gv_geom* g, const gv_tracks* tracks, const int32_t* node, gv_precision prec,
                       double* step, double* safety, int32_t* next, gv_workspace* ws, void* stream);
 
+/* --- transport loop (Physics subsection) -------------------------------------
+ * Each track is followed from its start point until it leaves the world, is absorbed
+ * or has taken kmax steps.  Per step, in the volume v it is in: the geometry gives the
+ * distance dgeo to the next boundary (the navigation step above, binary64); for each of
+ * the two processes of v's material (0 scatter, 1 absorb) a physics step
+ * s_i = -ln(xi_i) lambda_i is sampled with lambda_i = 1 / (n sigma_i), the mean free
+ * path of Eq. 1 (sigma_n[2 m + i] = n sigma_i of material m in 1/mm; 0 = the process
+ * is absent), and the shortest is taken (ties: process 0), as the paper's step
+ * selection does.  If it is shorter than dgeo the track moves by it and the process
+ * acts: scatter turns the direction to (sin a cos b, sin a sin b, cos a) with
+ * cos a = 2 xi_2 - 1, b = 2 pi xi_3; absorb ends the track.  Otherwise the track moves
+ * to the boundary and is located again from the world at the probe point p + 1e-6 d
+ * (a boundary belongs to both sides); outside the world it has escaped.
+ * The random numbers are inputs: xi[(i kmax + k) 4 + j] in (0, 1] for step k of track
+ * i (the library draws none).  Outputs per track: end reason, steps taken, end point,
+ * path length (the sum of the steps), the node of the last step (-1 escaped), and tie = 1
+ * when some step's outcome hung on a near tie (physics step within 1e-9 (1 + dgeo) of
+ * dgeo, the two nearest boundaries as close, or a relocation probe on a surface) - such
+ * a track may legitimately differ from another evaluation of the same loop.
+ * All arrays are device arrays; node_material has one entry per node (a material index
+ * outside [0, nmat) ends the track as GV_LOST); async on `stream`. */
+enum { GV_ESCAPED = 0, GV_ABSORBED = 1, GV_TRUNCATED = 2, GV_LOST = 3 };
+typedef struct {
+  int8_t* reason;
+  int32_t* steps;
+  double *x, *y, *z;  /* end point */
+  double* path;
+  int32_t* last;
+  int8_t* tie;
+} gv_transport_out;
+gv_status gv_transport(const gv_geom* g, const gv_tracks* tracks, const int32_t* node0,
+                       const int32_t* node_material, const double* sigma_n, int32_t nmat,
+                       const double* xi, int32_t kmax, const gv_transport_out* out, void* stream);
+
 /* --- serving: continuous batching of navigation requests (Project goals, item 1:
  *     the scheduler keeps handing baskets to the geometry) --------------------
  * A request is n tracks in world coordinates; the service locates them and takes

@@ -80,6 +80,8 @@ def _load():
         lib.or_locate.restype = None
         lib.or_nav_step.argtypes = [p, i, p, p, p, p, i64] + [p] * 6 + [p, p, p, p, i]
         lib.or_nav_step.restype = None
+        lib.or_transport.argtypes = [p, i, p, p, p, p, p, p, i64] + [p] * 7 + [p, i] + [p] * 8 + [i]
+        lib.or_transport.restype = None
         _lib = lib
         return lib
 
@@ -204,6 +206,26 @@ class Geometry:
         _load().or_locate(*self._common(), len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(node),
                           int(threads or default_threads()))
         return node
+
+    def transport(self, x, y, z, dx, dy, dz, node0, node_material, sigma_n, xi, kmax, threads=None):
+        """Transport loop (Physics subsection; see or_transport): random numbers ``xi`` of
+        shape (n, kmax, 4) in (0, 1]; ``sigma_n`` (nmat, 2) = n sigma of the scatter and absorb
+        processes per material (1/mm); returns reason, steps, final point, path, last node, tie."""
+        x, y, z, dx, dy, dz = map(_f64, (x, y, z, dx, dy, dz))
+        n = len(x)
+        node0 = np.ascontiguousarray(node0, np.int32)
+        mat = np.ascontiguousarray(node_material, np.int32)
+        sig = _f64(np.asarray(sigma_n, np.float64).reshape(-1))
+        xi = _f64(np.asarray(xi, np.float64).reshape(-1))
+        assert xi.size == n * kmax * 4 and mat.size == self.nnodes
+        out = {"reason": np.empty(n, np.int8), "steps": np.empty(n, np.int32), "x": np.empty(n), "y": np.empty(n),
+               "z": np.empty(n), "path": np.empty(n), "last": np.empty(n, np.int32), "tie": np.empty(n, np.int8)}
+        _load().or_transport(*self._common(), _ptr(mat), _ptr(sig), n, _ptr(x), _ptr(y), _ptr(z), _ptr(dx),
+                             _ptr(dy), _ptr(dz), _ptr(node0), _ptr(xi), int(kmax), _ptr(out["reason"]),
+                             _ptr(out["steps"]), _ptr(out["x"]), _ptr(out["y"]), _ptr(out["z"]),
+                             _ptr(out["path"]), _ptr(out["last"]), _ptr(out["tie"]),
+                             int(threads or default_threads()))
+        return out
 
     def nav_step(self, x, y, z, dx, dy, dz, node, threads=None):
         x, y, z, dx, dy, dz = map(_f64, (x, y, z, dx, dy, dz))

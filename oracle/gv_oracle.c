@@ -6,8 +6,9 @@
  * the library.  Every quantity is IEEE binary64; the file is compiled with
  * -ffp-contract=off so that no multiply-add is fused.
  *
- * What it computes (the three questions of the VecGeom section, and the
- * navigation step of the Physics / Detector geometry subsections):
+ * What it computes (the three questions of the VecGeom section, the navigation step
+ * of the Physics / Detector geometry subsections, and the transport loop of the
+ * Physics subsection, see or_transport):
  *
  *   Each solid is a set of constraints g_i(p) (in mm, negative = satisfied).
  *   s(p) = max_i g_i(p) is the decision quantity.  The point is INSIDE if
@@ -478,6 +479,30 @@ static void to_local(const double* R, const double* t, const double p[3], const 
   }
 }
 
+/* Locate one point: -1 outside the world, else the deepest node reached by descending
+ * into the first daughter (in index order) that does not classify it as outside.
+ * *surface (may be NULL) is set when a classification on the way was SURFACE. */
+static int locate_one(const or_solid* solids, int nnodes, const int32_t* node_solid, const int32_t* parent,
+                      const double* RG, const double* tg, const double p[3], int* surface) {
+  double pl[3];
+  to_local(RG, tg, p, NULL, pl, NULL);
+  int c0 = or_inside(&solids[node_solid[0]], pl);
+  if (surface && c0 == OR_SURFACE) *surface = 1;
+  if (c0 == OR_OUTSIDE) return -1;
+  int v = 0, moved = 1;
+  while (moved) {
+    moved = 0;
+    for (int c = 0; c < nnodes; c++) {
+      if (parent[c] != v) continue;
+      to_local(RG + 9 * c, tg + 3 * c, p, NULL, pl, NULL);
+      const int code = or_inside(&solids[node_solid[c]], pl);
+      if (surface && code == OR_SURFACE) *surface = 1;
+      if (code != OR_OUTSIDE) { v = c; moved = 1; break; }
+    }
+  }
+  return v;
+}
+
 void or_locate(const or_solid* solids, int nnodes, const int32_t* node_solid,
                const int32_t* parent, const double* RG, const double* tg,
                int64_t n, const double* x, const double* y, const double* z,
@@ -486,20 +511,41 @@ void or_locate(const or_solid* solids, int nnodes, const int32_t* node_solid,
 #pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
   for (int64_t i = 0; i < n; i++) {
     const double p[3] = {x[i], y[i], z[i]};
-    double pl[3];
-    to_local(RG, tg, p, NULL, pl, NULL);
-    if (or_inside(&solids[node_solid[0]], pl) == OR_OUTSIDE) { node[i] = -1; continue; }
-    int v = 0, moved = 1;
-    while (moved) {
-      moved = 0;
-      for (int c = 0; c < nnodes; c++) {
-        if (parent[c] != v) continue;
-        to_local(RG + 9 * c, tg + 3 * c, p, NULL, pl, NULL);
-        if (or_inside(&solids[node_solid[c]], pl) != OR_OUTSIDE) { v = c; moved = 1; break; }
-      }
-    }
-    node[i] = v;
+    node[i] = locate_one(solids, nnodes, node_solid, parent, RG, tg, p, NULL);
   }
+}
+
+/* The geometry half of a step for one track in node v: the distance to the next
+ * boundary (mother exit or first daughter entry), the safety, and the daughter entered
+ * (-1: the track leaves v).  *second (may be NULL) is the next smaller candidate. */
+static void nav_one(const or_solid* solids, int nnodes, const int32_t* node_solid, const int32_t* parent,
+                    const double* RG, const double* tg, const double p[3], const double d[3], int v,
+                    double* step, double* safety, int* next, double* second) {
+  double pl[3], dl[3];
+  to_local(RG + 9 * v, tg + 3 * v, p, d, pl, dl);
+  const or_solid* m = &solids[node_solid[v]];
+  double best = or_dist_out(m, pl, dl), runner = INFINITY;
+  int who = -1, have = best >= 0;
+  double saf = or_safety_out(m, pl);
+  int have_s = saf >= 0;
+  for (int c = 0; c < nnodes; c++) {
+    if (parent[c] != v) continue;
+    to_local(RG + 9 * c, tg + 3 * c, p, d, pl, dl);
+    const or_solid* ds = &solids[node_solid[c]];
+    const double t = or_dist_in(ds, pl, dl);
+    if (t >= 0 && (!have || t < best || (t == best && who == -1))) {
+      if (have && best < runner) runner = best;
+      best = t; who = c; have = 1;
+    } else if (t >= 0 && t < runner) {
+      runner = t;
+    }
+    const double sd = or_safety_in(ds, pl);
+    if (sd >= 0 && (!have_s || sd < saf)) { saf = sd; have_s = 1; }
+  }
+  *step = have ? best : -1.0;
+  if (safety) *safety = have_s ? saf : -1.0;
+  *next = have ? who : -1;
+  if (second) *second = runner;
 }
 
 void or_nav_step(const or_solid* solids, int nnodes, const int32_t* node_solid,
@@ -513,24 +559,81 @@ void or_nav_step(const or_solid* solids, int nnodes, const int32_t* node_solid,
     const double p[3] = {x[i], y[i], z[i]}, d[3] = {dx[i], dy[i], dz[i]};
     const int v = node[i];
     if (v < 0 || v >= nnodes) { step[i] = -1.0; safety[i] = -1.0; next[i] = -1; continue; }
-    double pl[3], dl[3];
-    to_local(RG + 9 * v, tg + 3 * v, p, d, pl, dl);
-    const or_solid* m = &solids[node_solid[v]];
-    double best = or_dist_out(m, pl, dl);
-    int who = -1, have = best >= 0;
-    double saf = or_safety_out(m, pl);
-    int have_s = saf >= 0;
-    for (int c = 0; c < nnodes; c++) {
-      if (parent[c] != v) continue;
-      to_local(RG + 9 * c, tg + 3 * c, p, d, pl, dl);
-      const or_solid* ds = &solids[node_solid[c]];
-      const double t = or_dist_in(ds, pl, dl);
-      if (t >= 0 && (!have || t < best || (t == best && who == -1))) { best = t; who = c; have = 1; }
-      const double sd = or_safety_in(ds, pl);
-      if (sd >= 0 && (!have_s || sd < saf)) { saf = sd; have_s = 1; }
+    int who;
+    nav_one(solids, nnodes, node_solid, parent, RG, tg, p, d, v, &step[i], &safety[i], &who, NULL);
+    next[i] = who;
+  }
+}
+
+/* ---------------------------------------------------------- transport loop */
+
+/* The transport of one track until it leaves the world, is absorbed, or has taken kmax
+ * steps (Physics subsection).  Per step, in the volume v the track is in:
+ *   - the geometry gives the distance dgeo to the next boundary (nav_one);
+ *   - for each of the two processes of v's material (0 scatter, 1 absorb) a step
+ *     s_i = -ln(xi_i) lambda_i is sampled, lambda_i = 1 / (n sigma_i) the mean free path
+ *     (Eq. 1; sigma_n[2 m + i] = n sigma_i of material m, 0 = process absent), and the
+ *     shortest is the candidate (ties: process 0);
+ *   - if it is shorter than dgeo the track moves by it and the process acts: scatter
+ *     turns the direction to (sin a cos b, sin a sin b, cos a) with cos a = 2 xi_2 - 1,
+ *     b = 2 pi xi_3; absorb ends the track;
+ *   - otherwise the track moves to the boundary and is located again from the world at
+ *     the probe point p + kPush d (the boundary itself belongs to both sides); outside
+ *     the world it has escaped.
+ * The random numbers are inputs: xi[(i kmax + k) 4 + j] in (0, 1] for step k.  A step
+ * whose outcome hangs on a near tie (physics against geometry, the two nearest
+ * boundaries, or a probe on a surface) marks the track in tie[i] (results stay valid). */
+#define OR_PUSH 1e-6
+void or_transport(const or_solid* solids, int nnodes, const int32_t* node_solid,
+                  const int32_t* parent, const double* RG, const double* tg,
+                  const int32_t* node_material, const double* sigma_n,
+                  int64_t n, const double* x, const double* y, const double* z,
+                  const double* dx, const double* dy, const double* dz, const int32_t* node0,
+                  const double* xi, int kmax, int8_t* reason, int32_t* nsteps, double* xo,
+                  double* yo, double* zo, double* path, int32_t* last, int8_t* tie, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+  for (int64_t i = 0; i < n; i++) {
+    double p[3] = {x[i], y[i], z[i]}, d[3] = {dx[i], dy[i], dz[i]};
+    int v = node0[i], k = 0, why = OR_TRUNCATED, near = 0;
+    double len = 0.0;
+    if (v < 0) why = OR_ESCAPED;
+    while (v >= 0 && k < kmax) {
+      const double* r = xi + ((size_t)i * (size_t)kmax + (size_t)k) * 4;
+      double dgeo, second;
+      int next;
+      nav_one(solids, nnodes, node_solid, parent, RG, tg, p, d, v, &dgeo, NULL, &next, &second);
+      if (dgeo < 0) { why = OR_LOST; break; }
+      const int m = node_material[v];
+      const double s0 = sigma_n[2 * m] > 0 ? -log(r[0]) / sigma_n[2 * m] : INFINITY;
+      const double s1 = sigma_n[2 * m + 1] > 0 ? -log(r[1]) / sigma_n[2 * m + 1] : INFINITY;
+      const int proc = s1 < s0 ? 1 : 0;
+      const double sp = proc ? s1 : s0;
+      const double scale = 1.0 + dgeo;
+      if (fabs(sp - dgeo) <= 1e-9 * scale || fabs(second - dgeo) <= 1e-9 * scale) near = 1;
+      k++;
+      if (sp < dgeo) {
+        for (int j = 0; j < 3; j++) p[j] = p[j] + sp * d[j];
+        len += sp;
+        if (proc == 1) { why = OR_ABSORBED; break; }
+        const double ca = 2.0 * r[2] - 1.0, b = 6.283185307179586 * r[3];  /* 2 pi */
+        const double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
+        d[0] = sa * cos(b); d[1] = sa * sin(b); d[2] = ca;
+      } else {
+        for (int j = 0; j < 3; j++) p[j] = p[j] + dgeo * d[j];
+        len += dgeo;
+        const double q[3] = {p[0] + OR_PUSH * d[0], p[1] + OR_PUSH * d[1], p[2] + OR_PUSH * d[2]};
+        int surf = 0;
+        v = locate_one(solids, nnodes, node_solid, parent, RG, tg, q, &surf);
+        if (surf) near = 1;
+        if (v < 0) { why = OR_ESCAPED; break; }
+      }
     }
-    step[i] = have ? best : -1.0;
-    safety[i] = have_s ? saf : -1.0;
-    next[i] = have ? who : -1;
+    reason[i] = (int8_t)why;
+    nsteps[i] = k;
+    xo[i] = p[0]; yo[i] = p[1]; zo[i] = p[2];
+    path[i] = len;
+    last[i] = why == OR_ESCAPED ? -1 : v;
+    tie[i] = (int8_t)near;
   }
 }

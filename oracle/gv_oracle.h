@@ -85,4 +85,13 @@ void or_nav_step(const or_solid* solids, int nnodes, const int32_t* node_solid,
                  int64_t n, const double* x, const double* y, const double* z,
                  const double* dx, const double* dy, const double* dz, const int32_t* node,
                  double* step, double* safety, int32_t* next, int nthreads);
+/* Transport loop: see gv_oracle.c.  End reasons: */
+enum { OR_ESCAPED = 0, OR_ABSORBED = 1, OR_TRUNCATED = 2, OR_LOST = 3 };
+void or_transport(const or_solid* solids, int nnodes, const int32_t* node_solid,
+                  const int32_t* node_parent, const double* R_global, const double* t_global,
+                  const int32_t* node_material, const double* sigma_n,
+                  int64_t n, const double* x, const double* y, const double* z,
+                  const double* dx, const double* dy, const double* dz, const int32_t* node0,
+                  const double* xi, int kmax, int8_t* reason, int32_t* nsteps, double* xo,
+                  double* yo, double* zo, double* path, int32_t* last, int8_t* tie, int nthreads);
 #endif

@@ -282,6 +282,34 @@ class Geometry:
                                 _ptr(out["safety"]), _ptr(out["next"]), ws, _stream_ptr(stream)))
         return out
 
+    def transport(self, tracks: dict, node0, node_material, sigma_n, xi, kmax: int, out: dict | None = None,
+                  stream=None) -> dict:
+        """The transport loop (gv_transport): CUDA tensors; ``node_material`` int32 per node,
+        ``sigma_n`` float64 (nmat, 2), ``xi`` float64 (n, kmax, 4) in (0, 1]."""
+        import torch
+        n = tracks["x"].numel()
+        dev = tracks["x"].device
+        if out is None:
+            out = {"reason": torch.empty(n, dtype=torch.int8, device=dev),
+                   "steps": torch.empty(n, dtype=torch.int32, device=dev),
+                   "x": torch.empty(n, dtype=torch.float64, device=dev),
+                   "y": torch.empty(n, dtype=torch.float64, device=dev),
+                   "z": torch.empty(n, dtype=torch.float64, device=dev),
+                   "path": torch.empty(n, dtype=torch.float64, device=dev),
+                   "last": torch.empty(n, dtype=torch.int32, device=dev),
+                   "tie": torch.empty(n, dtype=torch.int8, device=dev)}
+        if xi.numel() != n * kmax * 4 or node_material.numel() != self.nnodes or sigma_n.numel() % 2:
+            raise ValueError("transport: xi must hold n * kmax * 4 numbers, node_material one per node")
+        for tns in (node0, node_material, sigma_n, xi):
+            if not tns.is_cuda or not tns.is_contiguous():
+                raise ValueError("transport: expected contiguous CUDA tensors")
+        t = tracks_struct(tracks)
+        o = _abi.TransportOut(*(_ptr(out[k]) for k in ("reason", "steps", "x", "y", "z", "path", "last", "tie")))
+        check(lib().gv_transport(self.handle, ctypes.byref(t), _ptr(node0), _ptr(node_material), _ptr(sigma_n),
+                                 int(sigma_n.numel() // 2), _ptr(xi), int(kmax), ctypes.byref(o),
+                                 _stream_ptr(stream)))
+        return out
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value and _abi._lib is not None:

@@ -53,6 +53,12 @@ class Results(ctypes.Structure):
 
 # symbol -> (restype, argtypes); the CPU test checks that every declaration of
 # include/gv.h appears here and is exported by the library.
+class TransportOut(ctypes.Structure):
+    _fields_ = [("reason", ctypes.c_void_p), ("steps", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("path", ctypes.c_void_p),
+                ("last", ctypes.c_void_p), ("tie", ctypes.c_void_p)]
+
+
 SIGNATURES = {
     "gv_solid_box": (_i, [_d, _d, _d, _p]),
     "gv_solid_trd": (_i, [_d, _d, _d, _d, _d, _p]),
@@ -82,6 +88,8 @@ SIGNATURES = {
     "gv_geom_node_count": (ctypes.c_int32, [_p]),
     "gv_nav_locate": (_i, [_p, ctypes.POINTER(Tracks), _p, _p]),
     "gv_nav_step": (_i, [_p, ctypes.POINTER(Tracks), _p, _i, _p, _p, _p, _p, _p]),
+    "gv_transport": (_i, [_p, ctypes.POINTER(Tracks), _p, _p, _p, ctypes.c_int32, _p, ctypes.c_int32,
+                          ctypes.POINTER(TransportOut), _p]),
     "gv_server_create": (_i, [_p, ctypes.POINTER(ServerConfig), _p]),
     "gv_server_submit": (_i, [_p, _i64, _p, _p, _p]),
     "gv_server_poll": (_i, [_p, _i64, _p]),

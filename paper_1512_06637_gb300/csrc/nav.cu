@@ -326,6 +326,139 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
   }
 }
 
+// ------------------------------------------------------------ transport loop
+
+// Locate one point (as locate64) and report whether any classification on the way was
+// SURFACE (the point lies on a boundary within the tolerance).
+__device__ inline int32_t locate64_surf(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                        const Desc* __restrict__ solids, double x, double y, double z, bool& surf) {
+  f64::Track T{0, 0, 0, 0, 0, 0};
+  f64::Result R;
+  to_local64(nodes[0], x, y, z, T.x, T.y, T.z);
+  query64(solids[nodes[0].desc], T, f64::kWantCode, R);
+  surf |= R.code == 1;
+  if (R.code == 2) return -1;
+  int32_t v = 0;
+  for (int depth = 0; depth < 64; depth++) {
+    const NodeD& N = nodes[v];
+    int32_t into = -1;
+    for (int j = 0; j < N.count; j++) {
+      const int32_t c = children[N.first + j];
+      to_local64(nodes[c], x, y, z, T.x, T.y, T.z);
+      query64(solids[nodes[c].desc], T, f64::kWantCode, R);
+      surf |= R.code == 1;
+      if (R.code != 2) { into = c; break; }
+    }
+    if (into < 0) break;
+    v = into;
+  }
+  return v;
+}
+
+// The geometry half of a step for one point in node v (as nav_step64, without the
+// safety), and the next smaller candidate distance.
+__device__ inline void nav_one64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                 const Desc* __restrict__ solids, int32_t v, const double p[3], const double d[3],
+                                 double& step, int32_t& next, double& second) {
+  const NodeD& N = nodes[v];
+  f64::Track T;
+  f64::Result R;
+  to_local64(N, p[0], p[1], p[2], T.x, T.y, T.z);
+  rot_local64(N, d[0], d[1], d[2], T.u, T.v, T.w);
+  query64(solids[N.desc], T, f64::kWantDout, R);
+  double best = R.dout, runner = CUDART_INF;
+  bool have = best >= 0;
+  int32_t who = -1;
+  for (int j = 0; j < N.count; j++) {
+    const int32_t c = children[N.first + j];
+    const NodeD& C = nodes[c];
+    to_local64(C, p[0], p[1], p[2], T.x, T.y, T.z);
+    rot_local64(C, d[0], d[1], d[2], T.u, T.v, T.w);
+    query64(solids[C.desc], T, f64::kWantDin, R);
+    const double t = R.din;
+    if (t >= 0 && (!have || t < best || (t == best && who == -1))) {
+      if (have && best < runner) runner = best;
+      best = t; who = c; have = true;
+    } else if (t >= 0 && t < runner) {
+      runner = t;
+    }
+  }
+  step = have ? best : -1.0;
+  next = have ? who : -1;
+  second = runner;
+}
+
+struct TransportArgs {
+  const double *x, *y, *z, *u, *v, *w;  // start points and directions
+  const int32_t* node0;                 // start volumes
+  const int32_t* material;              // material of every node
+  const double* sigma_n;                // n sigma of (scatter, absorb) per material, 1/mm
+  const double* xi;                     // random numbers, [n][kmax][4], in (0, 1]
+  int32_t kmax, nmat, nnodes;
+  int8_t* reason;
+  int32_t* steps;
+  double *xo, *yo, *zo, *path;
+  int32_t* last;
+  int8_t* tie;
+  int64_t n;
+};
+
+constexpr double kPush = 1e-6;  // probe distance past a boundary for the relocation (mm)
+
+// One thread per track, binary64; the loop of the Physics subsection (see gv.h).
+__global__ void __launch_bounds__(256) k_transport(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                                   const Desc* __restrict__ solids, TransportArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    double p[3] = {a.x[i], a.y[i], a.z[i]}, d[3] = {a.u[i], a.v[i], a.w[i]};
+    int32_t v = a.node0[i];
+    int k = 0, why = GV_TRUNCATED;
+    bool near = false;
+    double len = 0.0;
+    if (v < 0 || v >= a.nnodes) why = v < 0 ? GV_ESCAPED : GV_LOST;
+    while (v >= 0 && v < a.nnodes && k < a.kmax) {
+      const double* r = a.xi + ((size_t)i * (size_t)a.kmax + (size_t)k) * 4;
+      double dgeo, second;
+      int32_t next;
+      nav_one64(nodes, children, solids, v, p, d, dgeo, next, second);
+      const int32_t m = a.material[v];
+      if (dgeo < 0 || m < 0 || m >= a.nmat) { why = GV_LOST; break; }
+      const double sig0 = a.sigma_n[2 * m], sig1 = a.sigma_n[2 * m + 1];
+      const double s0 = sig0 > 0 ? -log(r[0]) / sig0 : CUDART_INF;
+      const double s1 = sig1 > 0 ? -log(r[1]) / sig1 : CUDART_INF;
+      const int proc = s1 < s0 ? 1 : 0;
+      const double sp = proc ? s1 : s0;
+      const double scale = 1.0 + dgeo;
+      if (fabs(sp - dgeo) <= 1e-9 * scale || fabs(second - dgeo) <= 1e-9 * scale) near = true;
+      k++;
+      if (sp < dgeo) {  // the process acts before the boundary
+        for (int j = 0; j < 3; j++) p[j] = xadd(p[j], xmul(sp, d[j]));
+        len = xadd(len, sp);
+        if (proc == 1) { why = GV_ABSORBED; break; }
+        const double ca = xsub(xmul(2.0, r[2]), 1.0), b = xmul(6.283185307179586, r[3]);
+        const double sa = sqrt(fmax(0.0, xsub(1.0, xmul(ca, ca))));
+        double sb, cb;
+        sincos(b, &sb, &cb);
+        d[0] = xmul(sa, cb); d[1] = xmul(sa, sb); d[2] = ca;
+      } else {  // to the boundary, then locate the probe point past it
+        for (int j = 0; j < 3; j++) p[j] = xadd(p[j], xmul(dgeo, d[j]));
+        len = xadd(len, dgeo);
+        bool surf = false;
+        v = locate64_surf(nodes, children, solids, xadd(p[0], xmul(kPush, d[0])), xadd(p[1], xmul(kPush, d[1])),
+                          xadd(p[2], xmul(kPush, d[2])), surf);
+        near |= surf;
+        if (v < 0) { why = GV_ESCAPED; break; }
+      }
+    }
+    a.reason[i] = (int8_t)why;
+    a.steps[i] = k;
+    a.xo[i] = p[0]; a.yo[i] = p[1]; a.zo[i] = p[2];
+    a.path[i] = len;
+    a.last[i] = why == GV_ESCAPED ? -1 : v;
+    a.tie[i] = near ? 1 : 0;
+  }
+}
+
 }  // namespace gv
 
 using namespace gv;
@@ -460,6 +593,29 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GV_OK : cuda_error(e, "nav launch");
+}
+
+gv_status gv_transport(const gv_geom* g, const gv_tracks* t, const int32_t* node0, const int32_t* node_material,
+                       const double* sigma_n, int32_t nmat, const double* xi, int32_t kmax,
+                       const gv_transport_out* out, void* stream) {
+  if (!g || !t || !out) return set_error(GV_ERR_INVALID_ARG, "transport: NULL geometry, tracks or outputs");
+  if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "transport: negative track count");
+  if (kmax < 1 || nmat < 1) return set_error(GV_ERR_INVALID_ARG, "transport: kmax and nmat must be >= 1");
+  if (t->n == 0) return GV_OK;
+  if (!t->x || !t->y || !t->z || !t->dx || !t->dy || !t->dz || !node0 || !node_material || !sigma_n || !xi ||
+      !out->reason || !out->steps || !out->x || !out->y || !out->z || !out->path || !out->last || !out->tie)
+    return set_error(GV_ERR_INVALID_ARG, "transport: NULL array");
+  const void* ptrs[11] = {t->x, t->y, t->z, t->dx, t->dy, t->dz, sigma_n, xi, out->x, out->y, out->path};
+  for (int i = 0; i < 11; i++)
+    if ((uintptr_t)ptrs[i] & 7u) return set_error(GV_ERR_INVALID_ARG, "transport: arrays must be 8-byte aligned");
+  if ((uintptr_t)out->z & 7u) return set_error(GV_ERR_INVALID_ARG, "transport: arrays must be 8-byte aligned");
+  TransportArgs a{t->x, t->y, t->z, t->dx, t->dy, t->dz, node0, node_material, sigma_n, xi, kmax, nmat, g->nnodes,
+                  out->reason, out->steps, out->x, out->y, out->z, out->path, out->last, out->tie, t->n};
+  const int sms = sm_count();
+  const int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sms * 8);
+  k_transport<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, a);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GV_OK : cuda_error(e, "transport launch");
 }
 
 }  // extern "C"

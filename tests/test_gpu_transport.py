@@ -1,0 +1,90 @@
+"""The device transport loop (gv_transport) against the oracle's loop on the same tracks,
+materials and random numbers: end reason, number of steps and last volume identical and end
+point and path length within 1e-7 mm for every track that neither side marks as hanging on a
+near tie; ties are rare; edge cases (one step allowed, tracks starting outside the world,
+vacuum everywhere, a material index out of range)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests.helpers import to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gv():
+    import torch  # noqa: F401
+    import paper_1512_06637_gb300 as gv
+    from paper_1512_06637_gb300 import build
+    build.build()
+    return gv
+
+
+@pytest.fixture(scope="module")
+def geo():
+    return W.nested_geometry()
+
+
+def run_both(gv, geo, tr, node0, mat, sig, xi, kmax, with_oracle=True):
+    import torch
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    out = G.transport(to_device(tr, torch), torch.from_numpy(node0).cuda(), torch.from_numpy(mat).cuda(),
+                      torch.from_numpy(np.ascontiguousarray(sig, np.float64)).cuda(),
+                      torch.from_numpy(np.ascontiguousarray(xi)).cuda(), kmax)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    if not with_oracle:
+        return got, None
+    want = oracle.Geometry(geo["solids"], geo["nodes"]).transport(
+        tr["x"], tr["y"], tr["z"], tr["dx"], tr["dy"], tr["dz"], node0, mat, sig, xi, kmax)
+    return got, want
+
+
+def check(got, want, tol=1e-7):
+    sure = (got["tie"] == 0) & (want["tie"] == 0)
+    for k in ("reason", "steps", "last"):
+        bad = np.nonzero(sure & (got[k] != want[k]))[0]
+        assert len(bad) == 0, (k, bad[:5], got[k][bad[:5]], want[k][bad[:5]])
+    for k in ("x", "y", "z", "path"):
+        err = np.abs(got[k] - want[k])[sure]
+        assert (err <= tol + 1e-9 * np.abs(want[k][sure])).all(), (k, err.max())
+    return 1.0 - sure.mean()
+
+
+@pytest.mark.parametrize("kmax", [64, 1])
+def test_transport_matches_oracle(gv, geo, kmax):
+    n = 20011
+    tr = W.nested_tracks(n, seed=31, geom=geo)
+    node0 = oracle.Geometry(geo["solids"], geo["nodes"]).locate(tr["x"], tr["y"], tr["z"])
+    m = W.transport_materials(geo)
+    xi = W.transport_xi(n, kmax, seed=3)
+    got, want = run_both(gv, geo, tr, node0, m["node_material"], m["sigma_n"], xi, kmax)
+    tie_frac = check(got, want)
+    print(f"kmax {kmax}: reasons {np.bincount(got['reason'], minlength=4)}, mean steps {got['steps'].mean():.2f}, "
+          f"tie fraction {tie_frac:.5f}")
+    assert tie_frac < 0.01
+    if kmax == 1:
+        assert (got["steps"] <= 1).all()
+    else:
+        assert (np.bincount(got["reason"], minlength=4)[:2] > 0).all()   # some escape, some are absorbed
+
+
+def test_transport_edges(gv, geo):
+    n = 4099
+    tr = W.nested_tracks(n, seed=32, geom=geo)
+    G = oracle.Geometry(geo["solids"], geo["nodes"])
+    node0 = G.locate(tr["x"], tr["y"], tr["z"])
+    node0[::7] = -1                                   # starts outside the world: escaped, no step
+    nn = len(geo["nodes"])
+    xi = W.transport_xi(n, 16, seed=4)
+    vac = np.zeros(nn, np.int32)
+    got, want = run_both(gv, geo, tr, node0, vac, np.zeros((1, 2)), xi, 16)
+    check(got, want)
+    assert (got["reason"][::7] == 0).all() and (got["steps"][::7] == 0).all()
+    assert (got["reason"] != 1).all()                 # vacuum absorbs nothing
+    bad = np.full(nn, 5, np.int32)                    # material index out of range
+    got, _ = run_both(gv, geo, tr, node0, bad, np.zeros((1, 2)), xi, 16, with_oracle=False)
+    inside = node0 >= 0
+    assert (got["reason"][inside] == 3).all()

@@ -33,6 +33,14 @@ MUTANTS = {
     "rotation not transposed": ("pl[i] = (R[0 * 3 + i] * v[0] + R[1 * 3 + i] * v[1]) + R[2 * 3 + i] * v[2];",
                                 "pl[i] = (R[i * 3 + 0] * v[0] + R[i * 3 + 1] * v[1]) + R[i * 3 + 2] * v[2];"),
     "daughter tie rule dropped": ("(t == best && who == -1)", "(t == best && who != -1)"),
+    "absorption never acts": ("if (proc == 1) { why = OR_ABSORBED; break; }",
+                              "if (proc == 2) { why = OR_ABSORBED; break; }"),
+    "mean free path inverted": ("-log(r[1]) / sigma_n[2 * m + 1]", "-log(r[1]) * sigma_n[2 * m + 1]"),
+    "scatter cosine from the wrong number": ("const double ca = 2.0 * r[2] - 1.0", "const double ca = 2.0 * r[3] - 1.0"),
+    "relocation without the push": ("const double q[3] = {p[0] + OR_PUSH * d[0], p[1] + OR_PUSH * d[1], p[2] + OR_PUSH * d[2]};",
+                                    "const double q[3] = {p[0], p[1], p[2]};"),
+    "boundary step shortened": ("for (int j = 0; j < 3; j++) p[j] = p[j] + dgeo * d[j];",
+                                "for (int j = 0; j < 3; j++) p[j] = p[j] + 0.5 * dgeo * d[j];"),
 }
 
 

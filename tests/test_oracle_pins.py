@@ -484,3 +484,107 @@ def test_nav_tie_rules():
     assert r["step"][0] == 4.0 and r["next"][0] == 2           # lower index among equal daughters
     r = geo.nav_step(zero, zero, zero, zero, -one, zero, np.zeros(1, np.int32))
     assert r["step"][0] == 10.0 and r["next"][0] == -1         # leaves through the mother
+
+
+# ------------------------------------------------------------ transport loop
+
+def _box_world(D):
+    return oracle.Geometry([{"kind": "box", "params": tuple(D)}],
+                           [{"solid": 0, "parent": -1, "R": np.eye(3), "t": np.zeros(3)}])
+
+
+def test_transport_absorber_closed_form():
+    """One box of absorber (no scatter): a track is absorbed after s = -ln(xi_1) / (n sigma)
+    if that is shorter than its straight exit distance (slab method), else it escapes there."""
+    D = np.array([30.0, 20.0, 10.0])
+    geo = _box_world(D)
+    n, kmax, sig = 600, 4, 0.05
+    g = np.random.default_rng(71)
+    P = g.uniform(-1, 1, (n, 3)) * D * 0.999
+    d = W.isotropic(n, g)
+    xi = 1.0 - g.random((n, kmax, 4))
+    r = geo.transport(P[:, 0], P[:, 1], P[:, 2], d[:, 0], d[:, 1], d[:, 2], np.zeros(n, np.int32),
+                      np.zeros(1, np.int32), [[0.0, sig]], xi, kmax)
+    for i in range(n):
+        t_exit = _slab(D, P[i], d[i])[1]
+        s = -math.log(xi[i, 0, 1]) / sig
+        absorbed = s < t_exit
+        assert r["reason"][i] == (1 if absorbed else 0)
+        assert r["steps"][i] == 1
+        L = min(s, t_exit)
+        assert r["path"][i] == pytest.approx(L, rel=1e-12, abs=1e-9)
+        end = P[i] + L * d[i]
+        assert np.allclose([r["x"][i], r["y"][i], r["z"][i]], end, rtol=0, atol=1e-9)
+        assert r["last"][i] == (0 if absorbed else -1)
+
+
+def test_transport_scatter_two_steps_closed_form():
+    """A scatterer box with the random numbers chosen so that the first step scatters after
+    exactly a mm (xi_0 = exp(-a n sigma)) and the second leaves the box: the end point is
+    p + a d0 + t_exit(d1) d1 with d1 = (sin u cos v, sin u sin v, cos u), cos u = 2 xi_2 - 1,
+    v = 2 pi xi_3."""
+    D = np.array([40.0, 40.0, 40.0])
+    geo = _box_world(D)
+    n, kmax, sig, a = 300, 2, 0.2, 1.5
+    g = np.random.default_rng(72)
+    P = g.uniform(-1, 1, (n, 3)) * 20.0
+    d0 = W.isotropic(n, g)
+    xi = np.empty((n, kmax, 4))
+    xi[:, 0, 0] = math.exp(-a * sig)
+    xi[:, 0, 1] = 0.5
+    xi[:, 0, 2:] = g.uniform(0.01, 0.99, (n, 2))
+    xi[:, 1, :] = 1e-300      # second physics step: -ln(1e-300) / sig = 3454 mm, beyond the box
+    r = geo.transport(P[:, 0], P[:, 1], P[:, 2], d0[:, 0], d0[:, 1], d0[:, 2], np.zeros(n, np.int32),
+                      np.zeros(1, np.int32), [[sig, 0.0]], xi, kmax)
+    for i in range(n):
+        q = P[i] + a * d0[i]
+        cu = 2.0 * xi[i, 0, 2] - 1.0
+        v = 2.0 * math.pi * xi[i, 0, 3]
+        su = math.sqrt(1.0 - cu * cu)
+        d1 = np.array([su * math.cos(v), su * math.sin(v), cu])
+        t_exit = _slab(D, q, d1)[1]
+        assert r["reason"][i] == 0 and r["steps"][i] == 2
+        assert r["path"][i] == pytest.approx(a + t_exit, rel=1e-12, abs=1e-9)
+        assert np.allclose([r["x"][i], r["y"][i], r["z"][i]], q + t_exit * d1, rtol=0, atol=1e-9)
+
+
+def test_transport_vacuum_crosses_every_boundary():
+    """No material anywhere: every track flies straight out of the nested detector; its path
+    is the straight exit distance from the world box (slab method) and it ends on the world's
+    surface; with one step allowed, a track whose first boundary is inside the world stops on
+    that boundary (truncated, its point on the surface of the volume it started in)."""
+    geo_spec = W.nested_geometry()
+    geo = oracle.Geometry(geo_spec["solids"], geo_spec["nodes"])
+    D = np.array(geo_spec["solids"][0]["params"])
+    n = 400
+    t = W.nested_tracks(n, seed=9, geom=geo_spec)
+    node = geo.locate(t["x"], t["y"], t["z"])
+    nn = len(geo_spec["nodes"])
+    xi = np.full((n, 64, 4), 0.5)
+    r = geo.transport(t["x"], t["y"], t["z"], t["dx"], t["dy"], t["dz"], node, np.zeros(nn, np.int32),
+                      [[0.0, 0.0]], xi, 64)
+    P = np.stack([t["x"], t["y"], t["z"]], 1)
+    Dd = np.stack([t["dx"], t["dy"], t["dz"]], 1)
+    for i in range(n):
+        t_exit = _slab(D, P[i], Dd[i])[1]
+        assert r["reason"][i] == 0
+        assert r["path"][i] == pytest.approx(t_exit, rel=1e-12, abs=1e-8)
+        end = np.array([r["x"][i], r["y"][i], r["z"][i]])
+        assert abs(np.max(np.abs(end) / D) - 1.0) < 1e-12
+    r1 = geo.transport(t["x"], t["y"], t["z"], t["dx"], t["dy"], t["dz"], node, np.zeros(nn, np.int32),
+                       [[0.0, 0.0]], xi[:, :1].copy(), 1)
+    solids = [oracle.Solid.from_spec(s) for s in geo_spec["solids"]]
+    trunc = r1["reason"] == 2
+    assert trunc.sum() > n // 4 and (r1["steps"] == 1).all()
+    for i in np.nonzero(trunc)[0][:80]:
+        v = node[i]
+        Rg, tg = geo.RG[v].reshape(3, 3), geo.tg[v]
+        pl = Rg.T @ (np.array([r1["x"][i], r1["y"][i], r1["z"][i]]) - tg)
+        code = solids[geo_spec["nodes"][v]["solid"]].inside(pl[None, :])[0]
+        on_daughter = False
+        for c in range(nn):
+            if geo_spec["nodes"][c]["parent"] == v:
+                Rc, tc = geo.RG[c].reshape(3, 3), geo.tg[c]
+                pc = Rc.T @ (np.array([r1["x"][i], r1["y"][i], r1["z"][i]]) - tc)
+                on_daughter |= solids[geo_spec["nodes"][c]["solid"]].inside(pc[None, :])[0] == 1
+        assert code == 1 or on_daughter

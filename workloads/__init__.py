@@ -362,6 +362,26 @@ def nested_tracks(n: int, seed: int, geom: dict | None = None) -> dict:
     return soa(pts, isotropic(n, g))
 
 
+def transport_materials(geom: dict) -> dict:
+    """Materials of the nested detector for the transport loop: the world is vacuum, the tube
+    shells a light material, the box cells a dense one; n sigma of (scatter, absorb) in 1/mm
+    (mean free paths 100 / 500 mm in the shells, 20 / 50 mm in the cells)."""
+    nodes = geom["nodes"]
+    mat = np.zeros(len(nodes), np.int32)
+    for i, nd in enumerate(nodes):
+        if nd["parent"] == 0:
+            mat[i] = 1
+        elif nd["parent"] > 0:
+            mat[i] = 2
+    sigma_n = np.array([[0.0, 0.0], [0.01, 0.002], [0.05, 0.02]])
+    return {"node_material": mat, "sigma_n": sigma_n}
+
+
+def transport_xi(n: int, kmax: int, seed: int) -> np.ndarray:
+    """Uniform random numbers in (0, 1] for the transport loop, shape (n, kmax, 4)."""
+    return 1.0 - rng(7000 + seed).random((n, kmax, 4))
+
+
 def request_sizes(n_req: int, seed: int, lo: int = 1, hi: int = 65536) -> np.ndarray:
     g = rng(5000 + seed)
     return np.clip(np.floor(np.exp(g.uniform(math.log(lo), math.log(hi), n_req))), lo, hi).astype(np.int64)
