@@ -58,6 +58,7 @@ def _load():
             lib = ctypes.CDLL(_SO)
         d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         lib.or_solid_size.restype = i
+        lib.or_bool_size.restype = i
         for name, args in [
             ("or_setup_box", [d, d, d, p]),
             ("or_setup_trap", [p, p]),
@@ -65,6 +66,7 @@ def _load():
             ("or_setup_tube", [d, d, d, d, d, p]),
             ("or_setup_cone", [d, d, d, d, d, d, d, p]),
             ("or_setup_pcon", [i, p, p, p, d, d, p]),
+            ("or_setup_bool", [i, p, p, p, p, p, p]),
         ]:
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = i
@@ -94,6 +96,9 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+BOOL_OPS = {"union": 0, "subtraction": 1, "intersection": 2}
+
+
 class Solid:
     """One solid, set up by the oracle's own constructors from user parameters."""
 
@@ -119,6 +124,14 @@ class Solid:
             z, rmin, rmax = _f64(z), _f64(rmin), _f64(rmax)
             rc = lib.or_setup_pcon(len(z), _ptr(z), _ptr(rmin), _ptr(rmax), float(sphi),
                                    float(dphi), self._buf)
+        elif kind == "boolean":
+            # (op, component a spec, component c spec, R (3x3, c placed in a), t (3))
+            op, sa, sc, R, t = params
+            self._parts = (Solid.from_spec(sa), Solid.from_spec(sc))
+            self._bool = ctypes.create_string_buffer(lib.or_bool_size())
+            R, t = _f64(np.asarray(R, np.float64).reshape(9)), _f64(np.asarray(t, np.float64).reshape(3))
+            rc = lib.or_setup_bool(BOOL_OPS[op], self._parts[0].handle, self._parts[1].handle, _ptr(R), _ptr(t),
+                                   self._bool, self._buf)
         else:
             raise ValueError(f"unknown solid kind {kind!r}")
         if rc != 0:

@@ -37,9 +37,48 @@
 #include <string.h>
 
 #define H OR_HALF_TOL
-#define MAXROOTS 512
+#define MAXROOTS 1024  /* two polycones of OR_MAXZ planes at most (booleans) */
 
 int or_solid_size(void) { return (int)sizeof(or_solid); }
+int or_bool_size(void) { return (int)sizeof(or_bool); }
+
+/* ------------------------------------------------------------ boolean solids */
+
+int or_setup_bool(int op, const or_solid* a, const or_solid* c, const double R[9], const double t[3],
+                  or_bool* b, or_solid* s) {
+  if (op < OR_UNION || op > OR_INTERSECTION || !a || !c) return -1;
+  if (a->type == OR_BOOL || c->type == OR_BOOL) return -1;  /* components are primitives */
+  for (int i = 0; i < 9; i++) if (!isfinite(R[i])) return -1;
+  for (int i = 0; i < 3; i++) if (!isfinite(t[i])) return -1;
+  memset(b, 0, sizeof(*b));
+  b->op = op;
+  b->a = *a;
+  b->c = *c;
+  memcpy(b->R, R, sizeof(b->R));
+  memcpy(b->t, t, sizeof(b->t));
+  memset(s, 0, sizeof(*s));
+  s->type = OR_BOOL;
+  s->family = 2;
+  s->bl = b;
+  return 0;
+}
+
+/* a's frame -> c's frame: p_c = R^T (p - t), d_c = R^T d */
+static void bool_to_c(const or_bool* b, const double p[3], const double d[3], double pc[3], double dc[3]) {
+  const double v[3] = {p[0] - b->t[0], p[1] - b->t[1], p[2] - b->t[2]};
+  for (int i = 0; i < 3; i++) {
+    pc[i] = (b->R[0 * 3 + i] * v[0] + b->R[1 * 3 + i] * v[1]) + b->R[2 * 3 + i] * v[2];
+    if (d) dc[i] = (b->R[0 * 3 + i] * d[0] + b->R[1 * 3 + i] * d[1]) + b->R[2 * 3 + i] * d[2];
+  }
+}
+
+/* The decision quantity of op(a, c) from those of its components: union min, intersection
+ * max, subtraction max(s_a, -s_c) (inside a and outside c). */
+static double bool_combine(int op, double sa, double sc) {
+  if (op == OR_UNION) return sa < sc ? sa : sc;
+  if (op == OR_INTERSECTION) return sa > sc ? sa : sc;
+  return sa > -sc ? sa : -sc;
+}
 
 /* ------------------------------------------------------------------ setup */
 
@@ -213,6 +252,11 @@ static double dmax(double a, double b) { return a > b ? a : b; }
 static double dmin(double a, double b) { return a < b ? a : b; }
 
 double or_s_code(const or_solid* s, const double p[3]) {
+  if (s->type == OR_BOOL) {
+    double pc[3];
+    bool_to_c(s->bl, p, NULL, pc, NULL);
+    return bool_combine(s->bl->op, or_s_code(&s->bl->a, p), or_s_code(&s->bl->c, pc));
+  }
   if (s->family == 0) {
     double v = plane_g(&s->pl[0], p);
     for (int i = 1; i < s->nplanes; i++) v = dmax(v, plane_g(&s->pl[i], p));
@@ -243,11 +287,39 @@ static int code_of(double v) { return v < -H ? OR_INSIDE : (v > H ? OR_OUTSIDE :
 
 int or_inside(const or_solid* s, const double p[3]) { return code_of(or_s_code(s, p)); }
 
+/* Safeties of op(a, c) from the components' own safeties (lower bounds on their
+ * distances): leaving a union means leaving every component the point is in, entering an
+ * intersection means entering every component it is outside of, a subtraction is a and
+ * not-c (SafetyToIn of not-c is SafetyToOut of c, and the reverse). */
+static double bool_safety(const or_bool* b, const double p[3], int to_in) {
+  double pc[3];
+  bool_to_c(b, p, NULL, pc, NULL);
+  const int ca = or_inside(&b->a, p), cc = or_inside(&b->c, pc);
+  const double sia = or_safety_in(&b->a, p), soa = or_safety_out(&b->a, p);
+  const double sic = or_safety_in(&b->c, pc), soc = or_safety_out(&b->c, pc);
+  double v = -INFINITY;
+  if (b->op == OR_UNION) {
+    if (to_in) return dmin(sia, sic);
+    if (ca == OR_INSIDE) v = dmax(v, soa);
+    if (cc == OR_INSIDE) v = dmax(v, soc);
+  } else if (b->op == OR_INTERSECTION) {
+    if (!to_in) return dmin(soa, soc);
+    if (ca == OR_OUTSIDE) v = dmax(v, sia);
+    if (cc == OR_OUTSIDE) v = dmax(v, sic);
+  } else {
+    if (!to_in) return dmin(soa, sic);
+    if (ca == OR_OUTSIDE) v = dmax(v, sia);
+    if (cc == OR_INSIDE) v = dmax(v, soc);
+  }
+  return v;
+}
+
 double or_safety_in(const or_solid* s, const double p[3]) {
   const double v = or_s_code(s, p);
   const int c = code_of(v);
   if (c == OR_INSIDE) return -1.0;
   if (c == OR_SURFACE) return 0.0;
+  if (s->type == OR_BOOL) return bool_safety(s->bl, p, 1);
   if (s->family == 0) return v;
   double best = s_closed(s, 0, p);
   for (int k = 1; k + 1 < s->nz; k++) best = dmin(best, s_closed(s, k, p));
@@ -259,6 +331,7 @@ double or_safety_out(const or_solid* s, const double p[3]) {
   const int c = code_of(v);
   if (c == OR_OUTSIDE) return -1.0;
   if (c == OR_SURFACE) return 0.0;
+  if (s->type == OR_BOOL) return bool_safety(s->bl, p, 0);
   if (s->family == 0) return -v;
   return -s_closed(s, section_of(s, p[2]), p);
 }
@@ -268,7 +341,34 @@ double or_safety_out(const or_solid* s, const double p[3]) {
 /* Over the constraints of s at p that lie within the band (g >= -h): does any
  * grow along d (leaving), and does every one shrink along d (entering)? */
 static void surface_motion(const or_solid* s, const double p[3], const double d[3],
+                           int* leaving, int* entering);
+
+/* A boolean surface point: over the components within the band |s_x| <= h, each with its
+ * own motion (the complement of c, for a subtraction, with entering and leaving swapped):
+ * a union is entered when some band component is entered and left when all are left; an
+ * intersection (and a subtraction, a n not-c) is entered when all are entered and left
+ * when some is left. */
+static void bool_motion(const or_bool* b, const double p[3], const double d[3], int* leaving, int* entering) {
+  double pc[3], dc[3];
+  bool_to_c(b, p, d, pc, dc);
+  const double sa = or_s_code(&b->a, p), sc = or_s_code(&b->c, pc);
+  int la = 0, ea = 0, lc = 0, ec = 0;
+  const int ba = fabs(sa) <= H, bc = fabs(sc) <= H;
+  if (ba) surface_motion(&b->a, p, d, &la, &ea);
+  if (bc) surface_motion(&b->c, pc, dc, &lc, &ec);
+  if (b->op == OR_SUBTRACTION) { const int tmp = lc; lc = ec; ec = tmp; }
+  if (b->op == OR_UNION) {
+    *entering = (ba && ea) || (bc && ec);
+    *leaving = (!ba || la) && (!bc || lc);
+  } else {
+    *entering = (!ba || ea) && (!bc || ec);
+    *leaving = (ba && la) || (bc && lc);
+  }
+}
+
+static void surface_motion(const or_solid* s, const double p[3], const double d[3],
                            int* leaving, int* entering) {
+  if (s->type == OR_BOOL) { bool_motion(s->bl, p, d, leaving, entering); return; }
   double g[8], gd[8];
   int m = 0;
   if (s->family == 0) {
@@ -348,7 +448,12 @@ static int cmp_double(const void* a, const void* b) {
 
 static int candidates(const or_solid* s, const double p[3], const double d[3], double* t) {
   int m = 0;
-  if (s->family == 0) {
+  if (s->type == OR_BOOL) {  /* every crossing of either component's surfaces */
+    double pc[3], dc[3];
+    bool_to_c(s->bl, p, d, pc, dc);
+    m = candidates(&s->bl->a, p, d, t);
+    m += candidates(&s->bl->c, pc, dc, t + m);
+  } else if (s->family == 0) {
     for (int i = 0; i < s->nplanes; i++) plane_root(s->pl[i].n, s->pl[i].c, p, d, t, &m);
   } else {
     for (int k = 0; k + 1 < s->nz; k++) {

@@ -24,21 +24,33 @@
 #define OR_MAXZ 64          /* largest polycone z-plane count */
 #define OR_HALF_TOL 0.5e-9  /* h = kTolerance / 2, kTolerance = 1e-9 mm */
 
-enum { OR_BOX = 0, OR_TRD = 1, OR_TRAP = 2, OR_TUBE = 3, OR_CONE = 4, OR_PCON = 5 };
+enum { OR_BOX = 0, OR_TRD = 1, OR_TRAP = 2, OR_TUBE = 3, OR_CONE = 4, OR_PCON = 5, OR_BOOL = 6 };
+enum { OR_UNION = 0, OR_SUBTRACTION = 1, OR_INTERSECTION = 2 };
 enum { OR_INSIDE = 0, OR_SURFACE = 1, OR_OUTSIDE = 2 };
 
 typedef struct { double n[3]; double c; } or_plane;             /* g = n.p - c       */
 typedef struct { double a, b, k; int present; } or_line;        /* R(z) = a z + b    */
 
+struct or_bool_s;
+
 typedef struct {
   int type;
   int family;                 /* 0 = planar (box/trd/trap), 1 = phi-segmented polycone */
+  const struct or_bool_s* bl; /* OR_BOOL: the two components and the placement */
   int nplanes; or_plane pl[6];
   int nz; double z[OR_MAXZ];
   or_line out[OR_MAXZ - 1], in[OR_MAXZ - 1];
   int has_phi, phi_wide;
   double ns[2], ne[2];        /* outward normals of the phi = sphi and phi = sphi+dphi planes */
 } or_solid;
+
+/* A boolean solid: op(a, c), c placed in a's frame by p_a = R p_c + t (row-major R);
+ * components are primitive solids (copied). */
+typedef struct or_bool_s {
+  int op;
+  or_solid a, c;
+  double R[9], t[3];
+} or_bool;
 
 /* Setup.  Return 0 on success, -1 on an invalid description. */
 int or_setup_box(double dx, double dy, double dz, or_solid* s);
@@ -50,6 +62,10 @@ int or_setup_cone(double rmin1, double rmax1, double rmin2, double rmax2, double
 int or_setup_pcon(int nz, const double* z, const double* rmin, const double* rmax,
                   double sphi, double dphi, or_solid* s);
 int or_solid_size(void);
+/* b must outlive s (s points to it). */
+int or_setup_bool(int op, const or_solid* a, const or_solid* c, const double R[9], const double t[3],
+                  or_bool* b, or_solid* s);
+int or_bool_size(void);
 
 /* Per-point queries (single track). */
 double or_s_code(const or_solid* s, const double p[3]);

@@ -39,6 +39,11 @@ MUTANTS = {
     "scatter cosine from the wrong number": ("const double ca = 2.0 * r[2] - 1.0", "const double ca = 2.0 * r[3] - 1.0"),
     "relocation without the push": ("const double q[3] = {p[0] + OR_PUSH * d[0], p[1] + OR_PUSH * d[1], p[2] + OR_PUSH * d[2]};",
                                     "const double q[3] = {p[0], p[1], p[2]};"),
+    "boolean union takes the max": ("if (op == OR_UNION) return sa < sc ? sa : sc;", "if (op == OR_UNION) return sa > sc ? sa : sc;"),
+    "boolean subtraction keeps c": ("return sa > -sc ? sa : -sc;", "return sa > sc ? sa : sc;"),
+    "boolean placement ignored": ("const double v[3] = {p[0] - b->t[0], p[1] - b->t[1], p[2] - b->t[2]};",
+                                  "const double v[3] = {p[0], p[1], p[2]};"),
+    "boolean union safety max": ("if (to_in) return dmin(sia, sic);", "if (to_in) return dmax(sia, sic);"),
     "boundary step shortened": ("for (int j = 0; j < 3; j++) p[j] = p[j] + dgeo * d[j];",
                                 "for (int j = 0; j < 3; j++) p[j] = p[j] + 0.5 * dgeo * d[j];"),
 }

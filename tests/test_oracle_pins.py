@@ -588,3 +588,121 @@ def test_transport_vacuum_crosses_every_boundary():
                 pc = Rc.T @ (np.array([r1["x"][i], r1["y"][i], r1["z"][i]]) - tc)
                 on_daughter |= solids[geo_spec["nodes"][c]["solid"]].inside(pc[None, :])[0] == 1
         assert code == 1 or on_daughter
+
+
+# ------------------------------------------------------------ boolean solids
+
+BOOL_SPECS = W.boolean_table(12, seed=2)
+
+
+def _bool(op, a, c, R=np.eye(3), t=(0.0, 0.0, 0.0)):
+    return {"kind": "boolean", "params": (op, a, c, np.asarray(R, float), np.asarray(t, float))}
+
+
+@pytest.mark.parametrize("kind", ["box", "tube", "polycone"])
+def test_boolean_identities(kind):
+    """A u A = A n A = A \\ (c far away) = A n (c holding A) = A, query for query."""
+    g = np.random.default_rng(81)
+    a = W.random_solid(kind, g, 5.0, 40.0)
+    far = {"kind": "box", "params": (1.0, 1.0, 1.0)}
+    big = {"kind": "box", "params": (500.0, 500.0, 500.0)}
+    t = W.tracks_for_solid(a, 800, seed=82)
+    want = sol(a).query(**t)
+    for spec in (_bool("union", a, a), _bool("intersection", a, a), _bool("subtraction", a, far, t=(1e3, 0, 0)),
+                 _bool("intersection", a, big)):
+        got = sol(spec).query(**t)
+        for k in want:
+            assert np.array_equal(got[k], want[k]) or np.allclose(got[k], want[k], rtol=0, atol=1e-12), (spec, k)
+
+
+def test_boolean_disjoint_boxes_closed_form():
+    """Two boxes far apart: the union is entered at the earlier of the two slab entries,
+    and a point inside one box leaves the union where it leaves that box."""
+    D1, D2, t2 = np.array([10.0, 8.0, 6.0]), np.array([5.0, 5.0, 5.0]), np.array([40.0, 3.0, -2.0])
+    spec = _bool("union", {"kind": "box", "params": tuple(D1)}, {"kind": "box", "params": tuple(D2)}, t=t2)
+    g = np.random.default_rng(83)
+    n = 500
+    P = g.uniform(-1, 1, (n, 3)) * np.array([60.0, 20.0, 20.0]) + np.array([20.0, 0, 0])
+    d = W.isotropic(n, g)
+    r = sol(spec).query(P[:, 0], P[:, 1], P[:, 2], d[:, 0], d[:, 1], d[:, 2])
+    for i in range(n):
+        a1, b1 = _slab(D1, P[i], d[i])
+        a2, b2 = _slab(D2, P[i] - t2, d[i])
+        in1, in2 = a1 < 0 < b1, a2 < 0 < b2
+        if r["inside"][i] == OUT:
+            cands = [a for a, b in ((a1, b1), (a2, b2)) if a < b and a > 0]
+            want = min(cands) if cands else np.inf
+            assert r["dist_in"][i] == pytest.approx(want, abs=1e-9) or (np.isinf(want) and np.isinf(r["dist_in"][i]))
+        elif r["inside"][i] == IN:
+            want = b1 if in1 else b2
+            assert in1 or in2
+            assert r["dist_out"][i] == pytest.approx(want, abs=1e-9)
+
+
+def test_boolean_box_with_hole_closed_form():
+    """A slab (box) minus a box-shaped hole through it along x: a point in the wall moving
+    along +x leaves the solid at the hole's face or the slab's far face."""
+    A = {"kind": "box", "params": (20.0, 20.0, 5.0)}
+    C = {"kind": "box", "params": (4.0, 4.0, 10.0)}
+    s = sol(_bool("subtraction", A, C))
+    g = np.random.default_rng(84)
+    n = 300
+    P = np.stack([g.uniform(-19, -5, n), g.uniform(-3, 3, n), g.uniform(-4, 4, n)], 1)
+    one, zero = np.ones(n), np.zeros(n)
+    r = s.query(P[:, 0], P[:, 1], P[:, 2], one, zero, zero)
+    assert (r["inside"] == IN).all()
+    assert np.allclose(r["dist_out"], -4.0 - P[:, 0], atol=1e-9)          # the hole's -x face
+    assert np.allclose(r["safety_out"], np.minimum.reduce([-4.0 - P[:, 0], 20.0 + P[:, 0], 5.0 - np.abs(P[:, 2])]),
+                       atol=1e-9)
+    q = np.stack([np.full(n, -4.0 + 1e-3), P[:, 1], P[:, 2]], 1)          # inside the hole
+    r2 = s.query(q[:, 0], q[:, 1], q[:, 2], one, zero, zero)
+    assert (r2["inside"] == OUT).all()
+    assert np.allclose(r2["dist_in"], 8.0 - 1e-3, atol=1e-9)                # re-enters at x = +4
+
+
+@pytest.mark.parametrize("idx", range(len(BOOL_SPECS)))
+def test_boolean_brute_force_ray_march(idx):
+    spec = BOOL_SPECS[idx]
+    s = sol(spec)
+    n = 200
+    t = W.tracks_for_solid(spec, n, seed=400 + idx, near_frac=0.0)
+    P = np.stack([t["x"], t["y"], t["z"]], 1)
+    D = np.stack([t["dx"], t["dy"], t["dz"]], 1)
+    r = s.query(**t)
+    hb = W.bounding_half(spec)
+    tmax = 2.0 * np.linalg.norm(hb * 2.0 + 1.0)
+    step = float(max(hb.min() / 200.0, 0.01))
+    out = r["inside"] == OUT
+    ins = r["inside"] == IN
+    te = _march(s, P[out], D[out], True, tmax, step)
+    tx = _march(s, P[ins], D[ins], False, tmax, step)
+    fin = np.isfinite(te)
+    assert (r["dist_in"][out][fin] <= te[fin] + 1e-9).all()
+    with np.errstate(invalid="ignore"):
+        agree_e = np.where(fin, np.abs(r["dist_in"][out] - te) <= 1e-9, np.isinf(r["dist_in"][out]))
+    agree_x = np.abs(r["dist_out"][ins] - tx) <= 1e-9
+    assert agree_e.mean() >= 0.98, agree_e.mean()
+    assert agree_x.mean() >= 0.98, agree_x.mean()
+
+
+@pytest.mark.parametrize("idx", range(0, len(BOOL_SPECS), 2))
+def test_boolean_safety_is_a_lower_bound(idx):
+    """As for the primitives: 0 <= safety <= every distance along 64 Fibonacci directions."""
+    spec = BOOL_SPECS[idx]
+    s = sol(spec)
+    n = 300
+    t = W.tracks_for_solid(spec, n, seed=500 + idx)
+    r = s.query(**t)
+    k = np.arange(64) + 0.5
+    th = np.arccos(1 - 2 * k / 64)
+    ph = math.pi * (1 + 5 ** 0.5) * k
+    fib = np.stack([np.cos(ph) * np.sin(th), np.sin(ph) * np.sin(th), np.cos(th)], 1)
+    rep = lambda a: np.repeat(a, 64)  # noqa: E731
+    tt = {"x": rep(t["x"]), "y": rep(t["y"]), "z": rep(t["z"]),
+          "dx": np.tile(fib[:, 0], n), "dy": np.tile(fib[:, 1], n), "dz": np.tile(fib[:, 2], n)}
+    rr = s.query(**tt)
+    din, dout = rr["dist_in"].reshape(n, 64), rr["dist_out"].reshape(n, 64)
+    out, ins = r["inside"] == OUT, r["inside"] == IN
+    assert (r["safety_in"][out] > 0).all() and (r["safety_out"][ins] > 0).all()
+    assert (r["safety_in"][out] <= din[out].min(axis=1) + 1e-9).all()
+    assert (r["safety_out"][ins] <= dout[ins].min(axis=1) + 1e-9).all()

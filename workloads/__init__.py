@@ -151,8 +151,45 @@ def _as_pcon(spec):
     return list(z), list(rmin), list(rmax), sphi, dphi
 
 
+def random_rotation(g: np.random.Generator) -> np.ndarray:
+    """A uniformly random proper rotation (QR of a Gaussian matrix, signs fixed)."""
+    q, r = np.linalg.qr(g.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def boolean_random(g: np.random.Generator, lo=5.0, hi=60.0, op: str | None = None) -> dict:
+    """op(a, c): two random primitives, c smaller, rotated at random and shifted by up to
+    0.3 of a's extent so that the two overlap."""
+    kinds = ("box", "trd", "trap", "tube", "cone", "polycone")
+    op = op or str(g.choice(["union", "subtraction", "intersection"]))
+    a = random_solid(str(g.choice(kinds)), g, lo, hi)
+    c = random_solid(str(g.choice(kinds)), g, lo, hi * 0.7)
+    R = random_rotation(g)
+    t = g.uniform(-0.3, 0.3, 3) * bounding_half(a)
+    return {"kind": "boolean", "params": (op, a, c, R, t)}
+
+
+def boolean_table(n: int = 24, seed: int = 9) -> list[dict]:
+    g = rng(8000 + seed)
+    ops = ("union", "subtraction", "intersection")
+    return [boolean_random(g, op=ops[i % 3]) for i in range(n)]
+
+
+def _bool_parts(spec):
+    op, a, c, R, t = spec["params"]
+    return op, a, c, np.asarray(R, np.float64).reshape(3, 3), np.asarray(t, np.float64).reshape(3)
+
+
 def bounding_half(spec) -> np.ndarray:
     """Half-lengths of an axis-aligned box around the origin that holds the solid."""
+    if spec["kind"] == "boolean":
+        _, a, c, R, t = _bool_parts(spec)
+        hc = bounding_half(c)
+        corners = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]) * hc
+        return np.maximum(bounding_half(a), np.abs(corners @ R.T + t).max(axis=0))
     if spec["kind"] in ("box", "trd", "trap"):
         v = _trap_vertices(_as_trap(spec))
         return np.abs(v).max(axis=0)
@@ -162,7 +199,12 @@ def bounding_half(spec) -> np.ndarray:
 
 
 def _sample_inside(spec, n, g):
-    """Points drawn from the solid's parametric interior (not uniform in volume)."""
+    """Points drawn from the solid's parametric interior (not uniform in volume).  For a
+    boolean: from either component's interior (placed), whatever the operation keeps."""
+    if spec["kind"] == "boolean":
+        _, a, c, R, t = _bool_parts(spec)
+        na = n // 2
+        return np.concatenate([_sample_inside(a, na, g), _sample_inside(c, n - na, g) @ R.T + t])
     if spec["kind"] in ("box", "trd", "trap"):
         v = _trap_vertices(_as_trap(spec))
         a, b, c = g.random(n), g.random(n), g.random(n)
@@ -187,6 +229,10 @@ def _sample_inside(spec, n, g):
 
 def _sample_surface(spec, n, g):
     """Points drawn on the solid's faces, face chosen with probability ~ its area."""
+    if spec["kind"] == "boolean":  # on either component's surface (placed)
+        _, a, c, R, t = _bool_parts(spec)
+        na = n // 2
+        return np.concatenate([_sample_surface(a, na, g), _sample_surface(c, n - na, g) @ R.T + t])
     if spec["kind"] in ("box", "trd", "trap"):
         v = _trap_vertices(_as_trap(spec))
         quads = [(0, 1, 3, 2), (4, 5, 7, 6), (0, 1, 5, 4), (2, 3, 7, 6), (0, 2, 6, 4), (1, 3, 7, 5)]
