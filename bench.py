@@ -327,6 +327,7 @@ def run_ours(args):
         line["batched"] = bench_batched(gv, torch, max(3, args.steps), peaks)
         line["nav"] = bench_nav(gv, torch, max(3, args.steps))
         line["transport"] = bench_transport(gv, torch)
+        line["boolean"] = bench_boolean(gv, torch)
         if rank == 0:
             line["serving"] = bench_serving(gv, torch)
     if rank == 0 and not args.no_cpu:
@@ -513,6 +514,21 @@ def bench_transport(gv, torch, reps=3, n=1 << 20, kmax=64):
     return {"workload": "nested detector, 2^20 tracks, kmax 64, binary64", "tracks_per_s": n / (ms * 1e-3),
             "steps_per_s": steps / (ms * 1e-3), "mean_steps": steps / n, "ms": ms,
             "reasons": torch.bincount(out["reason"].long(), minlength=4).tolist()}
+
+
+def bench_boolean(gv, torch, reps=5, n=1 << 20):
+    """Boolean solids (binary64): a union, a subtraction and an intersection of random
+    primitives, 2^20 tracks each, all five queries."""
+    res = {}
+    for spec in W.boolean_table(3, seed=13):
+        op = spec["params"][0]
+        dev = {k: torch.from_numpy(v).cuda() for k, v in W.tracks_for_solid(spec, n, seed=21).items()}
+        s = gv.Solid.from_spec(spec)
+        out = gv.alloc_results(n, "cuda")
+        ms = _timed(torch, lambda: gv.query(s, dev, precision="fp64", out=out), reps)
+        res[op] = {"components": [spec["params"][1]["kind"], spec["params"][2]["kind"]],
+                   "queries_per_s": n * N_QUERIES / (ms * 1e-3), "us": ms * 1e3}
+    return res
 
 
 def bench_batched(gv, torch, reps, peaks):

@@ -95,6 +95,21 @@ gv_status gv_solid_cone(double rmin1, double rmax1, double rmin2, double rmax2, 
  * arrays are host memory and are copied. */
 gv_status gv_solid_polycone(int nz, const double* z, const double* rmin, const double* rmax,
                             double sphi, double dphi, gv_solid** out);
+/* Boolean solid op(a, c) (Detector geometry subsection: composite elements built with
+ * boolean operations): c placed in a's frame by p_a = R p_c + t (R row-major, a rotation:
+ * orthonormal to 1e-9, determinant +1).  The components must be primitive solids; the
+ * boolean keeps its own copies, so a and c may be destroyed afterwards.  Semantics: the
+ * decision quantity is min(s_a, s_c) (union), max(s_a, s_c) (intersection) or
+ * max(s_a, -s_c) (subtraction, a without c); safeties combine the components' safeties
+ * (lower bounds); distances are the first crossing from outside to inside (inside to
+ * outside) of the combined set along the ray, a surface point entering (leaving) the
+ * boolean by its components' own motion having DistanceToIn (DistanceToOut) 0.
+ * Booleans are evaluated in binary64 only: GV_FP32_REFINE runs the binary64 pass on them
+ * and sends nothing to the worklist.  At most 96 pieces of the ray inside a component
+ * are kept (far more than any solid here can produce). */
+enum { GV_UNION = 0, GV_SUBTRACTION = 1, GV_INTERSECTION = 2 };
+gv_status gv_solid_boolean(int32_t op, const gv_solid* a, const gv_solid* c, const double R[9], const double t[3],
+                           gv_solid** out);
 void gv_solid_destroy(gv_solid* s);
 
 /* --- baskets ------------------------------------------------------------ */

@@ -21,6 +21,9 @@ def _f(v):
     return ctypes.c_double(float(v))
 
 
+BOOL_OPS = {"union": 0, "subtraction": 1, "intersection": 2}
+
+
 class Solid:
     """A solid handle owned by the library (immutable once created)."""
 
@@ -44,6 +47,13 @@ class Solid:
             n = len(z)
             arr = lambda v: (ctypes.c_double * n)(*map(float, v))  # noqa: E731
             st = L.gv_solid_polycone(n, arr(z), arr(rmin), arr(rmax), _f(sphi), _f(dphi), ctypes.byref(h))
+        elif kind == "boolean":
+            # (op, component a spec, component c spec, R (3x3, c placed in a), t (3))
+            op, sa, sc, R, t = params
+            a, c = Solid.from_spec(sa), Solid.from_spec(sc)  # the boolean keeps its own copies
+            Rv = (ctypes.c_double * 9)(*[float(v) for row in R for v in row])
+            tv = (ctypes.c_double * 3)(*map(float, t))
+            st = L.gv_solid_boolean(BOOL_OPS[op], a.handle, c.handle, Rv, tv, ctypes.byref(h))
         else:
             raise ValueError(f"unknown solid kind {kind!r}")
         check(st)

@@ -66,6 +66,7 @@ SIGNATURES = {
     "gv_solid_tube": (_i, [_d, _d, _d, _d, _d, _p]),
     "gv_solid_cone": (_i, [_d, _d, _d, _d, _d, _d, _d, _p]),
     "gv_solid_polycone": (_i, [_i, _p, _p, _p, _d, _d, _p]),
+    "gv_solid_boolean": (_i, [ctypes.c_int32, _p, _p, _p, _p, _p]),
     "gv_solid_destroy": (None, [_p]),
     "gv_workspace_create": (_i, [_i64, _p]),
     "gv_workspace_destroy": (None, [_p]),

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_batched(const Desc* 
           f64::Result R;
           if (type == kBox) f64::box_query(S, T, want, R);
           else if (type == kTrd || type == kTrap) f64::planar_query(S, T, want, R);
+          else if (type == kBool) f64::bool_query(S, T, want, R);
           else f64::pcon_query(S, T, want, R);
           if (a.inside) a.inside[i] = (int8_t)R.code;
           if (a.din) a.din[i] = R.din;
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_batched(const Desc* 
             if (type == kBox) f32::box32(S, T, want, R);
             else if (type == kTrd || type == kTrap) f32::planar32(S, T, want, R);
             else if (type == kTube) f32::pcon32<true>(S, T, want, R);
+            else if (type == kBool) R.flag = true;  // booleans: binary64 only
             else f32::pcon32<false>(S, T, want, R);
           }
           flag = R.flag;
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(256) k_batched_refine(const Desc* __restrict__
     f64::Result R;
     if (S.type == kBox) f64::box_query(S, T, want, R);
     else if (S.type == kTrd || S.type == kTrap) f64::planar_query(S, T, want, R);
+    else if (S.type == kBool) f64::bool_query(S, T, want, R);
     else f64::pcon_query(S, T, want, R);
     if (a.inside) a.inside[i] = (int8_t)R.code;
     if (a.din) a.din[i] = R.din;
@@ -323,10 +326,13 @@ gv_status gv_batch_create(const gv_solid* const* solids, int32_t nsolids, const 
   b->baskets.assign(baskets, baskets + nbaskets);
   b->tile_cap = std::max<int64_t>(tile_cap, 1);
   cudaError_t e = cudaGetDevice(&b->device);
-  std::vector<Desc> h(nsolids);
-  for (int i = 0; i < nsolids; i++) { h[i] = solids[i]->h; b->solid_types.push_back(h[i].type); }
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_solids, sizeof(Desc) * nsolids);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_solids, h.data(), sizeof(Desc) * nsolids, cudaMemcpyHostToDevice);
+  for (int i = 0; i < nsolids; i++) b->solid_types.push_back(solids[i]->h.type);
+  const int nrec = table_size(solids, nsolids);  // booleans carry their components along
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_solids, sizeof(Desc) * nrec);
+  if (e == cudaSuccess) {
+    const std::vector<Desc> h = table_records(solids, nsolids, b->d_solids);
+    e = cudaMemcpy(b->d_solids, h.data(), sizeof(Desc) * nrec, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(Tile) * b->tile_cap);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_next, 64);
   if (e == cudaSuccess) e = cudaMemset(b->d_next, 0, 64);

@@ -19,7 +19,8 @@
 
 namespace gv {
 
-enum SolidType : int32_t { kBox = 0, kTrd = 1, kTrap = 2, kTube = 3, kCone = 4, kPcon = 5 };
+enum SolidType : int32_t { kBox = 0, kTrd = 1, kTrap = 2, kTube = 3, kCone = 4, kPcon = 5, kBool = 6 };
+enum BoolOp : int32_t { kUnion = 0, kSubtraction = 1, kIntersection = 2 };
 
 constexpr int kMaxZ = 32;            // polycone z-planes (GV_MAX_ZPLANES)
 constexpr double kHalfTol = 0.5e-9;  // h = kTolerance / 2 (mm)
@@ -55,6 +56,14 @@ struct alignas(16) Desc {
   float oah[kMaxZ - 1], oal[kMaxZ - 1], obh[kMaxZ - 1], obl[kMaxZ - 1], ok_[kMaxZ - 1];
   float iah[kMaxZ - 1], ial[kMaxZ - 1], ibh[kMaxZ - 1], ibl[kMaxZ - 1], ik_[kMaxZ - 1];
   float size;                    // largest |coordinate| of the solid's extent (mm)
+
+  // Boolean solids (type kBool): op(a, c) with c placed in a's frame by
+  // p_a = bR p_c + bt (row-major); parts points to the two component records
+  // (device memory owned by the boolean's handle).
+  int32_t bop;
+  int32_t bpad;
+  double bR[9], bt[3];
+  const Desc* parts;
 };
 
 // Order-preserving integer key of a binary64 bit pattern: for non-NaN a, b,

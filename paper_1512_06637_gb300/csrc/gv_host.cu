@@ -210,6 +210,29 @@ static gv_status make_pcon(int type, int nz, const double* z, const double* rmin
 
 using namespace gv;
 
+namespace gv {
+
+int table_size(const gv_solid* const* solids, int n) {
+  int m = n;
+  for (int i = 0; i < n; i++) if (solids[i]->h.type == kBool) m += 2;
+  return m;
+}
+
+std::vector<Desc> table_records(const gv_solid* const* solids, int n, Desc* d_table) {
+  std::vector<Desc> recs;
+  recs.reserve(table_size(solids, n));
+  for (int i = 0; i < n; i++) recs.push_back(solids[i]->h);
+  for (int i = 0; i < n; i++) {
+    if (solids[i]->h.type != kBool) continue;
+    recs[i].parts = d_table + recs.size();
+    recs.push_back(solids[i]->ph[0]);
+    recs.push_back(solids[i]->ph[1]);
+  }
+  return recs;
+}
+
+}  // namespace gv
+
 extern "C" {
 
 gv_status gv_solid_box(double dx, double dy, double dz, gv_solid** out) {
@@ -248,6 +271,53 @@ gv_status gv_solid_cone(double rmin1, double rmax1, double rmin2, double rmax2, 
 gv_status gv_solid_polycone(int nz, const double* z, const double* rmin, const double* rmax, double sphi,
                             double dphi, gv_solid** out) {
   return make_pcon(kPcon, nz, z, rmin, rmax, sphi, dphi, out);
+}
+
+gv_status gv_solid_boolean(int32_t op, const gv_solid* a, const gv_solid* c, const double R[9], const double t[3],
+                           gv_solid** out) {
+  if (!out) return set_error(GV_ERR_INVALID_ARG, "out handle pointer is NULL");
+  if (!a || !c || !R || !t) return set_error(GV_ERR_INVALID_ARG, "boolean: NULL component or placement");
+  if (op != GV_UNION && op != GV_SUBTRACTION && op != GV_INTERSECTION)
+    return set_error(GV_ERR_INVALID_ARG, "boolean: unknown operation");
+  if (a->h.type == kBool || c->h.type == kBool)
+    return set_error(GV_ERR_UNSUPPORTED, "boolean: components must be primitive solids");
+  if (a->device != c->device) return set_error(GV_ERR_INVALID_ARG, "boolean: components on different devices");
+  for (int i = 0; i < 9; i++) if (!std::isfinite(R[i])) return set_error(GV_ERR_INVALID_ARG, "boolean: non-finite rotation");
+  for (int i = 0; i < 3; i++) if (!std::isfinite(t[i])) return set_error(GV_ERR_INVALID_ARG, "boolean: non-finite shift");
+  for (int i = 0; i < 3; i++)  // R must be a rotation: orthonormal rows, determinant +1
+    for (int j = 0; j < 3; j++) {
+      const double d = R[3 * i] * R[3 * j] + R[3 * i + 1] * R[3 * j + 1] + R[3 * i + 2] * R[3 * j + 2];
+      if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-9) return set_error(GV_ERR_INVALID_ARG, "boolean: R is not orthonormal");
+    }
+  const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                     R[2] * (R[3] * R[7] - R[4] * R[6]);
+  if (det < 0) return set_error(GV_ERR_INVALID_ARG, "boolean: R is a reflection");
+  gv_solid* s = new (std::nothrow) gv_solid;
+  if (!s) return set_error(GV_ERR_OUT_OF_MEMORY, "host allocation failed");
+  init_desc(s->h, kBool);
+  s->h.bop = op;
+  std::memcpy(s->h.bR, R, sizeof(s->h.bR));
+  std::memcpy(s->h.bt, t, sizeof(s->h.bt));
+  s->h.size = std::fmax(a->h.size, c->h.size);
+  s->ph[0] = a->h;
+  s->ph[1] = c->h;
+  s->d = nullptr;
+  s->device = a->device;
+  // one allocation: the boolean's record, then copies of the two component records
+  cudaError_t e = cudaMalloc(&s->d, 3 * sizeof(Desc));
+  if (e == cudaSuccess) {
+    s->h.parts = s->d + 1;
+    const Desc recs[3] = {s->h, a->h, c->h};
+    e = cudaMemcpy(s->d, recs, sizeof(recs), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    if (s->d) cudaFree(s->d);
+    delete s;
+    return e == cudaErrorMemoryAllocation ? set_error(GV_ERR_OUT_OF_MEMORY, "cudaMalloc of a solid failed")
+                                          : cuda_error(e, "boolean upload");
+  }
+  *out = s;
+  return GV_OK;
 }
 
 void gv_solid_destroy(gv_solid* s) {

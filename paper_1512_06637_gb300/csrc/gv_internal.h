@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 #include "gv.h"
 #include "gv_desc.h"
 
@@ -10,6 +11,7 @@ struct gv_solid {
   gv::Desc h;          // host copy
   gv::Desc* d;         // device copy (on `device`)
   int device;
+  gv::Desc ph[2];      // boolean: host copies of the two components
 };
 
 struct gv_workspace {
@@ -30,6 +32,13 @@ struct QueryArgs {
 };
 
 gv_status set_error(gv_status st, const std::string& msg);
+
+// Records of a device table of solids (a batch's or a geometry's): one per solid, then the
+// two component records of every boolean, whose parts pointer is set to them, so that the
+// table does not depend on the lifetime of the solids' handles.  d_table is the device
+// address the table will be copied to; returns the records to copy.
+std::vector<Desc> table_records(const gv_solid* const* solids, int n, Desc* d_table);
+int table_size(const gv_solid* const* solids, int n);
 gv_status cuda_error(cudaError_t e, const char* where);
 int sm_count();
 

@@ -79,6 +79,7 @@ __device__ __forceinline__ void rot_local64(const NodeD& N, double u, double v, 
 __device__ __forceinline__ void query64(const Desc& S, const f64::Track& T, unsigned want, f64::Result& R) {
   if (S.type == kBox) f64::box_query(S, T, want, R);
   else if (S.type == kTrd || S.type == kTrap) f64::planar_query(S, T, want, R);
+  else if (S.type == kBool) f64::bool_query(S, T, want, R);
   else f64::pcon_query(S, T, want, R);
 }
 
@@ -235,6 +236,7 @@ __device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, uns
   if (S.type == kBox) f32::box32<true>(S, T, want, R);
   else if (S.type == kTrd || S.type == kTrap) f32::planar32<true>(S, T, want, R);
   else if (S.type == kTube) f32::pcon32<true, true>(S, T, want, R);
+  else if (S.type == kBool) R.flag = true;  // booleans: binary64 only
   else f32::pcon32<false, true>(S, T, want, R);
 }
 
@@ -523,15 +525,16 @@ gv_status gv_geom_create(int32_t nnodes, const gv_solid* const* node_solid, cons
     g->children[g->nodes[p].first + fill[p]++] = v;
   }
   g->nsolids = (int)uniq.size();
-  for (const gv_solid* s : uniq) g->solids.push_back(s->h);
+  const int nrec = table_size(uniq.data(), g->nsolids);  // booleans carry their components along
   cudaError_t e = cudaGetDevice(&g->device);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_nodes, sizeof(NodeD) * nnodes);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_children, sizeof(int32_t) * g->children.size());
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_solids, sizeof(Desc) * g->nsolids);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_solids, sizeof(Desc) * nrec);
+  if (e == cudaSuccess) g->solids = table_records(uniq.data(), g->nsolids, g->d_solids);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_nodes, g->nodes.data(), sizeof(NodeD) * nnodes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(g->d_children, g->children.data(), sizeof(int32_t) * g->children.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(g->d_solids, g->solids.data(), sizeof(Desc) * g->nsolids, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_solids, g->solids.data(), sizeof(Desc) * nrec, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     gv_geom_destroy(g);
     return e == cudaErrorMemoryAllocation ? set_error(GV_ERR_OUT_OF_MEMORY, "geom: cudaMalloc failed") : cuda_error(e, "geom upload");

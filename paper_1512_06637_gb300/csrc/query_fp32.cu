@@ -191,6 +191,8 @@ cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* w
   // counter[0]: worklist length; counter[1]: next track of the lane-refill dispenser
   cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess || a.n == 0) return e;
+  // boolean solids have no binary32 pass: evaluated in binary64 (nothing goes to the worklist)
+  if (s->h.type == kBool) return launch_query_fp64(s, a, stream);
   const int threads = 256;
   int64_t blocks = (a.n + threads - 1) / threads;
   const int sms = sm_count();

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) k_query_fp64(const Desc* __restrict__ des
     f64::Result R;
     if (FAMILY == 0) f64::box_query(S, T, want, R);
     else if (FAMILY == 1) f64::planar_query(S, T, want, R);
+    else if (FAMILY == 4) f64::bool_query(S, T, want, R);
     else f64::pcon_query(S, T, want, R);
     if (a.inside) a.inside[i] = (int8_t)R.code;
     if (a.din) a.din[i] = R.din;
@@ -46,6 +47,7 @@ cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_
     case kBox: k_query_fp64<0><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a); break;
     case kTrd:
     case kTrap: k_query_fp64<1><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a); break;
+    case kBool: k_query_fp64<4><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a); break;
     default: k_query_fp64<2><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a); break;
   }
   return cudaGetLastError();

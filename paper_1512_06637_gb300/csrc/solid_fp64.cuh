@@ -419,11 +419,299 @@ __device__ inline void pcon_query(const Desc& S, const Track& T, unsigned want, 
   }
 }
 
+// ------------------------------------------------------------ boolean solids
+//
+// op(a, c) for two primitives, c placed in a's frame.  Codes and safeties come from the
+// components' decision quantities and safeties (union min / max, intersection max / min,
+// subtraction as a and not-c).  Distances come from the pieces of the ray inside each
+// component - the intervals of t on which the component's s <= 0, found from its surfaces
+// in closed form - combined with the set operation; the first piece starting after 0 is
+// the entry and the end of the piece holding 0+ (else of the first piece after 0) the exit.
+
+constexpr int kMaxPieces = 96;
+struct Pieces {
+  int n = 0;
+  bool over = false;
+  double a[kMaxPieces], b[kMaxPieces];
+  // pieces arrive in increasing t; a piece touching or overlapping the last is merged
+  __device__ __forceinline__ void push(double lo, double hi) {
+    if (!(lo < hi)) return;
+    if (n > 0 && lo <= b[n - 1]) {
+      if (hi > b[n - 1]) b[n - 1] = hi;
+      return;
+    }
+    if (n < kMaxPieces) { a[n] = lo; b[n] = hi; n++; } else over = true;
+  }
+};
+
+// constraint g + t gd <= 0 along the ray: clip [lo, hi]
+__device__ __forceinline__ void clip_le(double g, double gd, double& lo, double& hi) {
+  if (gd == 0) { if (g > 0) { lo = GV_INF; hi = -GV_INF; } return; }
+  const double t = -g / gd;
+  if (gd > 0) hi = dmin(hi, t); else lo = dmax(lo, t);
+}
+
+__device__ inline void planar_pieces(const Desc& S, const Track& T, Pieces& P) {
+  double lo = -GV_INF, hi = GV_INF;
+  if (S.type == kBox) {
+    const double p[3] = {T.x, T.y, T.z}, d[3] = {T.u, T.v, T.w};
+    for (int i = 0; i < 3; i++) {
+      clip_le(xsub(p[i], S.D[i]), d[i], lo, hi);            //  x - D <= 0
+      clip_le(xsub(-p[i], S.D[i]), -d[i], lo, hi);          // -x - D <= 0
+    }
+  } else {
+    for (int i = 0; i < 4; i++) {
+      const double* Q = S.pl[i];
+      clip_le(xsub(xadd(xadd(xmul(Q[0], T.x), xmul(Q[1], T.y)), xmul(Q[2], T.z)), Q[3]),
+              xadd(xadd(xmul(Q[0], T.u), xmul(Q[1], T.v)), xmul(Q[2], T.w)), lo, hi);
+    }
+    clip_le(xsub(T.z, S.dz), T.w, lo, hi);
+    clip_le(xsub(-T.z, S.dz), -T.w, lo, hi);
+  }
+  P.push(lo, hi);
+}
+
+// the region r <= a z + b (one nappe) of a section line along the ray
+__device__ __forceinline__ void cone_region(const Line& L, const Track& T, double r2, double radial, double A0,
+                                            double r, double& lo, double& hi) {
+  const Cross c = line_cross(L, T, r2, radial, A0);
+  if (c.hm || c.hp) {
+    lo = c.hm ? c.tm : -GV_INF;
+    hi = c.hp ? c.tp : GV_INF;
+  } else if (xsub(r, xadd(xmul(L.a, T.z), L.b)) <= 0) {  // no crossing: the whole line or nothing
+    lo = -GV_INF; hi = GV_INF;
+  } else {
+    lo = GV_INF; hi = -GV_INF;
+  }
+}
+
+// [lo, hi] minus (xlo, xhi): up to two pieces, pushed in order
+__device__ __forceinline__ int minus(double lo, double hi, double xlo, double xhi, double* oa, double* ob) {
+  if (!(xlo < xhi) || xhi <= lo || xlo >= hi) { oa[0] = lo; ob[0] = hi; return 1; }
+  int m = 0;
+  if (xlo > lo) { oa[m] = lo; ob[m] = xlo; m++; }
+  if (xhi < hi) { oa[m] = xhi; ob[m] = hi; m++; }
+  return m;
+}
+
+__device__ inline void pcon_pieces(const Desc& S, const Track& T, Pieces& P) {
+  const int last = S.nz - 1;
+  const double r2 = xadd(xmul(T.x, T.x), xmul(T.y, T.y));
+  const double r = __dsqrt_rn(r2);
+  const double radial = xadd(xmul(T.x, T.u), xmul(T.y, T.v));
+  const double A0 = xadd(xmul(T.u, T.u), xmul(T.v, T.v));
+  double plo = -GV_INF, phi_hi = GV_INF, xlo = GV_INF, xhi = -GV_INF;  // narrow phi; wide-phi wedge
+  if (S.flags & kHasPhi) {
+    const Phi f = phi_eval(S, T.x, T.y);
+    const double nds = xadd(xmul(S.ns[0], T.u), xmul(S.ns[1], T.v));
+    const double nde = xadd(xmul(S.ne[0], T.u), xmul(S.ne[1], T.v));
+    if (!(S.flags & kPhiWide)) {
+      clip_le(f.a, nds, plo, phi_hi);
+      clip_le(f.b, nde, plo, phi_hi);
+    } else {  // the wedge n_s.p > 0 and n_e.p > 0
+      xlo = -GV_INF; xhi = GV_INF;
+      clip_le(-f.a, -nds, xlo, xhi);
+      clip_le(-f.b, -nde, xlo, xhi);
+    }
+  }
+  const int kb = T.w < 0 ? last - 1 : 0, step = T.w < 0 ? -1 : 1;
+  for (int i = 0; i < last; i++) {
+    const int k = kb + step * i;
+    double slo, shi;
+    if (T.w > 0) { slo = (S.z[k] - T.z) / T.w; shi = (S.z[k + 1] - T.z) / T.w; }
+    else if (T.w < 0) { slo = (S.z[k + 1] - T.z) / T.w; shi = (S.z[k] - T.z) / T.w; }
+    else if (T.z >= S.z[k] && T.z <= S.z[k + 1]) { slo = -GV_INF; shi = GV_INF; }
+    else continue;
+    double lo, hi;
+    cone_region(S.out[k], T, r2, radial, A0, r, lo, hi);
+    lo = dmax(dmax(lo, slo), plo);
+    hi = dmin(dmin(hi, shi), phi_hi);
+    if (!(lo < hi)) continue;
+    double ha = GV_INF, hb = -GV_INF;  // the hole
+    if (inner_has(S, k)) cone_region(S.in[k], T, r2, radial, A0, r, ha, hb);
+    double a1[2], b1[2];
+    const int m1 = minus(lo, hi, ha, hb, a1, b1);
+    for (int j = 0; j < m1; j++) {
+      double a2[2], b2[2];
+      const int m2 = minus(a1[j], b1[j], xlo, xhi, a2, b2);
+      for (int q = 0; q < m2; q++) P.push(a2[q], b2[q]);
+    }
+  }
+}
+
+__device__ __forceinline__ void prim_pieces(const Desc& S, const Track& T, Pieces& P) {
+  if (S.type == kBox || S.type == kTrd || S.type == kTrap) planar_pieces(S, T, P);
+  else pcon_pieces(S, T, P);
+}
+
+__device__ __forceinline__ double prim_s(const Desc& S, double x, double y, double z) {
+  if (S.type == kBox) return box_s(S, x, y, z);
+  if (S.type == kTrd || S.type == kTrap) return planar_s(S, x, y, z);
+  return pcon_s(S, x, y, z);
+}
+
+// The surface motion of a primitive at its band (the rule its own query applies).
+__device__ inline Motion prim_motion(const Desc& S, const Track& T) {
+  Motion m;
+  if (S.type == kBox) {
+    const double p[3] = {T.x, T.y, T.z}, d[3] = {T.u, T.v, T.w};
+    for (int i = 0; i < 3; i++) m.add(xsub(fabs(p[i]), S.D[i]), p[i] < 0 ? -d[i] : d[i]);
+  } else if (S.type == kTrd || S.type == kTrap) {
+    for (int i = 0; i < 4; i++) {
+      const double* P = S.pl[i];
+      m.add(xsub(xadd(xadd(xmul(P[0], T.x), xmul(P[1], T.y)), xmul(P[2], T.z)), P[3]),
+            xadd(xadd(xmul(P[0], T.u), xmul(P[1], T.v)), xmul(P[2], T.w)));
+    }
+    m.add(xsub(fabs(T.z), S.dz), T.z < 0 ? -T.w : T.w);
+  } else {
+    const int last = S.nz - 1;
+    const double r = __dsqrt_rn(xadd(xmul(T.x, T.x), xmul(T.y, T.y)));
+    const int k0 = section_of(S, T.z);
+    const double radial = xadd(xmul(T.x, T.u), xmul(T.y, T.v));
+    m.add(g_out(S.out[k0], r, T.z), xsub(radial, xmul(xmul(S.out[k0].a, T.w), r)));
+    if (inner_has(S, k0)) m.add(g_in(S.in[k0], r, T.z), -xsub(radial, xmul(xmul(S.in[k0].a, T.w), r)));
+    m.add(xsub(S.z[0], T.z), -T.w);
+    m.add(xsub(T.z, S.z[last]), T.w);
+    if (S.flags & kHasPhi) {
+      const Phi f = phi_eval(S, T.x, T.y);
+      const double nds = xadd(xmul(S.ns[0], T.u), xmul(S.ns[1], T.v));
+      const double nde = xadd(xmul(S.ne[0], T.u), xmul(S.ne[1], T.v));
+      if (S.flags & kPhiWide) { if (f.a <= f.b) m.add(f.a, nds); else m.add(f.b, nde); }
+      else { m.add(f.a, nds); m.add(f.b, nde); }
+    }
+  }
+  return m;
+}
+
+__device__ inline void prim_query(const Desc& S, const Track& T, unsigned want, Result& R) {
+  switch (S.type) {
+    case kBox: box_query(S, T, want, R); break;
+    case kTrd:
+    case kTrap: planar_query(S, T, want, R); break;
+    default: pcon_query(S, T, want, R); break;
+  }
+}
+
+static __device__ __noinline__ void bool_query(const Desc& S, const Track& T, unsigned want, Result& R) {
+  const Desc& A = S.parts[0];
+  const Desc& C = S.parts[1];
+  Track Tc;  // c's frame: p_c = R^T (p - t), d_c = R^T d
+  {
+    const double v0 = xsub(T.x, S.bt[0]), v1 = xsub(T.y, S.bt[1]), v2 = xsub(T.z, S.bt[2]);
+    const double* M = S.bR;
+    Tc.x = xadd(xadd(xmul(M[0], v0), xmul(M[3], v1)), xmul(M[6], v2));
+    Tc.y = xadd(xadd(xmul(M[1], v0), xmul(M[4], v1)), xmul(M[7], v2));
+    Tc.z = xadd(xadd(xmul(M[2], v0), xmul(M[5], v1)), xmul(M[8], v2));
+    Tc.u = xadd(xadd(xmul(M[0], T.u), xmul(M[3], T.v)), xmul(M[6], T.w));
+    Tc.v = xadd(xadd(xmul(M[1], T.u), xmul(M[4], T.v)), xmul(M[7], T.w));
+    Tc.w = xadd(xadd(xmul(M[2], T.u), xmul(M[5], T.v)), xmul(M[8], T.w));
+  }
+  const int op = S.bop;
+  const double sa = prim_s(A, T.x, T.y, T.z), sc = prim_s(C, Tc.x, Tc.y, Tc.z);
+  const double s = op == kUnion ? dmin(sa, sc) : (op == kIntersection ? dmax(sa, sc) : dmax(sa, -sc));
+  R.code = code_of(s);
+  if (want & (kWantSin | kWantSout)) {
+    Result ra, rc;
+    prim_query(A, T, kWantCode | kWantSin | kWantSout, ra);
+    prim_query(C, Tc, kWantCode | kWantSin | kWantSout, rc);
+    double vin, vout;
+    if (op == kUnion) {
+      vin = dmin(ra.sin, rc.sin);
+      vout = -GV_INF;
+      if (ra.code == 0) vout = dmax(vout, ra.sout);
+      if (rc.code == 0) vout = dmax(vout, rc.sout);
+    } else if (op == kIntersection) {
+      vout = dmin(ra.sout, rc.sout);
+      vin = -GV_INF;
+      if (ra.code == 2) vin = dmax(vin, ra.sin);
+      if (rc.code == 2) vin = dmax(vin, rc.sin);
+    } else {
+      vout = dmin(ra.sout, rc.sin);
+      vin = -GV_INF;
+      if (ra.code == 2) vin = dmax(vin, ra.sin);
+      if (rc.code == 0) vin = dmax(vin, rc.sout);
+    }
+    finish_safety(R.code, vin, vout, R);
+  }
+  if (!(want & (kWantDin | kWantDout))) return;
+  // surface motion from the components within the band
+  bool entering = false, leaving = false;
+  if (R.code == 1) {
+    const bool ba = fabs(sa) <= H, bc = fabs(sc) <= H;
+    bool la = false, ea = false, lc = false, ec = false;
+    if (ba) { const Motion m = prim_motion(A, T); la = m.any_out; ea = m.all_in; }
+    if (bc) { const Motion m = prim_motion(C, Tc); lc = m.any_out; ec = m.all_in; }
+    if (op == kSubtraction) { const bool tmp = lc; lc = ec; ec = tmp; }
+    if (op == kUnion) {
+      entering = (ba && ea) || (bc && ec);
+      leaving = (!ba || la) && (!bc || lc);
+    } else {
+      entering = (!ba || ea) && (!bc || ec);
+      leaving = (ba && la) || (bc && lc);
+    }
+  }
+  Pieces pa, pc, pr;
+  prim_pieces(A, T, pa);
+  prim_pieces(C, Tc, pc);
+  if (op == kUnion) {  // merge in order of start
+    int i = 0, j = 0;
+    while (i < pa.n || j < pc.n) {
+      if (j >= pc.n || (i < pa.n && pa.a[i] <= pc.a[j])) { pr.push(pa.a[i], pa.b[i]); i++; }
+      else { pr.push(pc.a[j], pc.b[j]); j++; }
+    }
+  } else if (op == kIntersection) {
+    int i = 0, j = 0;
+    while (i < pa.n && j < pc.n) {
+      pr.push(dmax(pa.a[i], pc.a[j]), dmin(pa.b[i], pc.b[j]));
+      if (pa.b[i] < pc.b[j]) i++; else j++;
+    }
+  } else {  // a minus every piece of c
+    int j = 0;
+    for (int i = 0; i < pa.n; i++) {
+      double lo = pa.a[i];
+      const double hi = pa.b[i];
+      while (j < pc.n && pc.b[j] <= lo) j++;
+      int q = j;
+      while (q < pc.n && pc.a[q] < hi && lo < hi) {
+        if (pc.a[q] > lo) pr.push(lo, pc.a[q]);
+        lo = dmax(lo, pc.b[q]);
+        q++;
+      }
+      pr.push(lo, hi);
+    }
+  }
+  if (want & kWantDout) {
+    if (R.code == 2) R.dout = -1.0;
+    else if (R.code == 1 && leaving) R.dout = 0.0;
+    else {
+      double t = 0.0;  // a surface point whose ray never gets inside leaves at once
+      for (int i = 0; i < pr.n; i++) {
+        if (pr.b[i] <= 0) continue;
+        t = pr.b[i];  // the piece holding 0+, else the first one after 0
+        break;
+      }
+      R.dout = t;
+    }
+  }
+  if (want & kWantDin) {
+    if (R.code == 0) R.din = -1.0;
+    else if (R.code == 1 && entering) R.din = 0.0;
+    else {
+      double t = GV_INF;
+      for (int i = 0; i < pr.n; i++)
+        if (pr.a[i] > 0) { t = pr.a[i]; break; }
+      R.din = t;
+    }
+  }
+  if (pa.over || pc.over || pr.over) R.din = R.dout = nan("");
+}
+
 __device__ __forceinline__ void query(const Desc& S, const Track& T, unsigned want, Result& R) {
   switch (S.type) {
     case kBox: box_query(S, T, want, R); break;
     case kTrd:
     case kTrap: planar_query(S, T, want, R); break;
+    case kBool: bool_query(S, T, want, R); break;
     default: pcon_query(S, T, want, R); break;
   }
 }
