@@ -407,57 +407,110 @@ struct TransportArgs {
 
 constexpr double kPush = 1e-6;  // probe distance past a boundary for the relocation (mm)
 
-// One thread per track, binary64; the loop of the Physics subsection (see gv.h).
+// The state of one track in the loop.
+struct Flight {
+  double p[3], d[3], len;
+  int32_t v, k, why;
+  bool near, live;
+};
+
+__device__ __forceinline__ void flight_begin(const TransportArgs& a, int64_t i, Flight& F) {
+  F.p[0] = a.x[i]; F.p[1] = a.y[i]; F.p[2] = a.z[i];
+  F.d[0] = a.u[i]; F.d[1] = a.v[i]; F.d[2] = a.w[i];
+  F.v = a.node0[i];
+  F.k = 0;
+  F.why = GV_TRUNCATED;
+  F.near = false;
+  F.len = 0.0;
+  F.live = F.v >= 0 && F.v < a.nnodes && a.kmax > 0;
+  if (F.v < 0) F.why = GV_ESCAPED;
+  else if (F.v >= a.nnodes) F.why = GV_LOST;
+}
+
+// One step of the loop of the Physics subsection (see gv.h) for track i.
+__device__ inline void flight_step(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                   const Desc* __restrict__ solids, const TransportArgs& a, int64_t i, Flight& F) {
+  const double* r = a.xi + ((size_t)i * (size_t)a.kmax + (size_t)F.k) * 4;
+  double dgeo, second;
+  int32_t next;
+  nav_one64(nodes, children, solids, F.v, F.p, F.d, dgeo, next, second);
+  const int32_t m = a.material[F.v];
+  if (dgeo < 0 || m < 0 || m >= a.nmat) { F.why = GV_LOST; F.live = false; return; }
+  const double sig0 = a.sigma_n[2 * m], sig1 = a.sigma_n[2 * m + 1];
+  const double s0 = sig0 > 0 ? -log(r[0]) / sig0 : CUDART_INF;
+  const double s1 = sig1 > 0 ? -log(r[1]) / sig1 : CUDART_INF;
+  const int proc = s1 < s0 ? 1 : 0;
+  const double sp = proc ? s1 : s0;
+  const double scale = 1.0 + dgeo;
+  if (fabs(sp - dgeo) <= 1e-9 * scale || fabs(second - dgeo) <= 1e-9 * scale) F.near = true;
+  F.k++;
+  if (sp < dgeo) {  // the process acts before the boundary
+    for (int j = 0; j < 3; j++) F.p[j] = xadd(F.p[j], xmul(sp, F.d[j]));
+    F.len = xadd(F.len, sp);
+    if (proc == 1) { F.why = GV_ABSORBED; F.live = false; return; }
+    const double ca = xsub(xmul(2.0, r[2]), 1.0), b = xmul(6.283185307179586, r[3]);
+    const double sa = sqrt(fmax(0.0, xsub(1.0, xmul(ca, ca))));
+    double sb, cb;
+    sincos(b, &sb, &cb);
+    F.d[0] = xmul(sa, cb); F.d[1] = xmul(sa, sb); F.d[2] = ca;
+  } else {  // to the boundary, then locate the probe point past it
+    for (int j = 0; j < 3; j++) F.p[j] = xadd(F.p[j], xmul(dgeo, F.d[j]));
+    F.len = xadd(F.len, dgeo);
+    bool surf = false;
+    F.v = locate64_surf(nodes, children, solids, xadd(F.p[0], xmul(kPush, F.d[0])),
+                        xadd(F.p[1], xmul(kPush, F.d[1])), xadd(F.p[2], xmul(kPush, F.d[2])), surf);
+    F.near |= surf;
+    if (F.v < 0) { F.why = GV_ESCAPED; F.live = false; return; }
+  }
+  if (F.k >= a.kmax) F.live = false;  // truncated
+}
+
+__device__ __forceinline__ void flight_end(const TransportArgs& a, int64_t i, const Flight& F) {
+  a.reason[i] = (int8_t)F.why;
+  a.steps[i] = F.k;
+  a.xo[i] = F.p[0]; a.yo[i] = F.p[1]; a.zo[i] = F.p[2];
+  a.path[i] = F.len;
+  a.last[i] = F.why == GV_ESCAPED ? -1 : F.v;
+  a.tie[i] = F.near ? 1 : 0;
+}
+
+// Binary64, lane refill: tracks take from one to kmax steps, so each warp owns a
+// contiguous range of tracks and keeps one in each lane; when at least half its lanes are
+// idle they take the next tracks of the range, then every busy lane takes one step.
 __global__ void __launch_bounds__(256) k_transport(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                    const Desc* __restrict__ solids, TransportArgs a) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    double p[3] = {a.x[i], a.y[i], a.z[i]}, d[3] = {a.u[i], a.v[i], a.w[i]};
-    int32_t v = a.node0[i];
-    int k = 0, why = GV_TRUNCATED;
-    bool near = false;
-    double len = 0.0;
-    if (v < 0 || v >= a.nnodes) why = v < 0 ? GV_ESCAPED : GV_LOST;
-    while (v >= 0 && v < a.nnodes && k < a.kmax) {
-      const double* r = a.xi + ((size_t)i * (size_t)a.kmax + (size_t)k) * 4;
-      double dgeo, second;
-      int32_t next;
-      nav_one64(nodes, children, solids, v, p, d, dgeo, next, second);
-      const int32_t m = a.material[v];
-      if (dgeo < 0 || m < 0 || m >= a.nmat) { why = GV_LOST; break; }
-      const double sig0 = a.sigma_n[2 * m], sig1 = a.sigma_n[2 * m + 1];
-      const double s0 = sig0 > 0 ? -log(r[0]) / sig0 : CUDART_INF;
-      const double s1 = sig1 > 0 ? -log(r[1]) / sig1 : CUDART_INF;
-      const int proc = s1 < s0 ? 1 : 0;
-      const double sp = proc ? s1 : s0;
-      const double scale = 1.0 + dgeo;
-      if (fabs(sp - dgeo) <= 1e-9 * scale || fabs(second - dgeo) <= 1e-9 * scale) near = true;
-      k++;
-      if (sp < dgeo) {  // the process acts before the boundary
-        for (int j = 0; j < 3; j++) p[j] = xadd(p[j], xmul(sp, d[j]));
-        len = xadd(len, sp);
-        if (proc == 1) { why = GV_ABSORBED; break; }
-        const double ca = xsub(xmul(2.0, r[2]), 1.0), b = xmul(6.283185307179586, r[3]);
-        const double sa = sqrt(fmax(0.0, xsub(1.0, xmul(ca, ca))));
-        double sb, cb;
-        sincos(b, &sb, &cb);
-        d[0] = xmul(sa, cb); d[1] = xmul(sa, sb); d[2] = ca;
-      } else {  // to the boundary, then locate the probe point past it
-        for (int j = 0; j < 3; j++) p[j] = xadd(p[j], xmul(dgeo, d[j]));
-        len = xadd(len, dgeo);
-        bool surf = false;
-        v = locate64_surf(nodes, children, solids, xadd(p[0], xmul(kPush, d[0])), xadd(p[1], xmul(kPush, d[1])),
-                          xadd(p[2], xmul(kPush, d[2])), surf);
-        near |= surf;
-        if (v < 0) { why = GV_ESCAPED; break; }
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int64_t chunk = (a.n + nwarps - 1) / nwarps;
+  const int64_t end = (warp + 1) * chunk < a.n ? (warp + 1) * chunk : a.n;
+  int64_t next = warp * chunk;  // warp-uniform
+  const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
+  bool busy = false;
+  int64_t i = 0;
+  Flight F;
+  while (true) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !busy);
+    if (next < end && (__popc(idle) >= 16 || idle == 0xffffffffu)) {
+      const int64_t j = next + __popc(idle & below);
+      next += __popc(idle);
+      if (!busy && j < end) {
+        i = j;
+        flight_begin(a, i, F);
+        busy = F.live;
+        if (!busy) flight_end(a, i, F);
       }
     }
-    a.reason[i] = (int8_t)why;
-    a.steps[i] = k;
-    a.xo[i] = p[0]; a.yo[i] = p[1]; a.zo[i] = p[2];
-    a.path[i] = len;
-    a.last[i] = why == GV_ESCAPED ? -1 : v;
-    a.tie[i] = near ? 1 : 0;
+    if (__ballot_sync(0xffffffffu, busy) == 0u) {
+      if (next >= end) break;
+      continue;
+    }
+    if (busy) {
+      flight_step(nodes, children, solids, a, i, F);
+      if (!F.live) {
+        flight_end(a, i, F);
+        busy = false;
+      }
+    }
   }
 }
 
