@@ -328,6 +328,7 @@ def run_ours(args):
         line["nav"] = bench_nav(gv, torch, max(3, args.steps))
         line["transport"] = bench_transport(gv, torch)
         line["boolean"] = bench_boolean(gv, torch)
+        line["voxels"] = bench_voxels(gv, torch)
         if rank == 0:
             line["serving"] = bench_serving(gv, torch)
     if rank == 0 and not args.no_cpu:
@@ -578,6 +579,51 @@ def bench_nav(gv, torch, reps, n=1 << 22):
         if prec == "fp32_refine":
             res[prec]["refined_fraction"] = ws.refined() / n
     res["locate_ms"] = _timed(torch, lambda: G.locate(dev, out=node), max(1, reps // 2))
+    return res
+
+
+def bench_voxels(gv, torch, reps=3, n=1 << 20, n_transport=1 << 18, kmax=32):
+    """Voxelised navigation: the crowded lattice (1728 daughters of the world, one holding 27
+    more), 2^20 tracks uniform in the world (10% along an axis), located once; locate, one
+    binary64 step, one binary32 + refinement step (each with and without the safety, which
+    is a minimum over every daughter), and the transport loop (2^18 tracks, kmax 32,
+    binary64) with the daughters' grids on and off."""
+    geo = W.crowded_geometry()
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    dev = {k: torch.from_numpy(v).cuda() for k, v in W.crowded_tracks(geo, n, seed=2, surf_frac=0.0).items()}
+    node = G.locate(dev)
+    ws = gv.Workspace(n)
+    out = G.step(dev, node, precision="fp64", workspace=ws)
+    tdev = {k: v[:n_transport].contiguous() for k, v in dev.items()}
+    node0 = node[:n_transport].contiguous()
+    m = W.crowded_materials(geo)
+    mat = torch.from_numpy(m["node_material"]).cuda()
+    sig = torch.from_numpy(m["sigma_n"]).cuda()
+    xi = torch.from_numpy(W.transport_xi(n_transport, kmax, seed=2)).cuda()
+    tout = G.transport(tdev, node0, mat, sig, xi, kmax)
+    res = {"workload": "crowded lattice, 1728 + 27 daughters, 2^20 tracks; transport 2^18 tracks, kmax 32",
+           "grids": G.voxel_count}
+    for on in (True, False):
+        G.set_voxels(on)
+        r = max(1, reps if on else 1)
+        key = "grids" if on else "brute_force"
+        res[key] = {
+            "locate_ms": _timed(torch, lambda: G.locate(dev, out=node), r),
+            "fp64_step_ms": _timed(torch, lambda: G.step(dev, node, precision="fp64", workspace=ws, out=out), r),
+            "fp32_refine_step_ms": _timed(torch, lambda: G.step(dev, node, precision="fp32_refine", workspace=ws,
+                                                                out=out), r),
+            "fp64_step_nosafety_ms": _timed(torch, lambda: G.step(dev, node, precision="fp64", workspace=ws, out=out,
+                                                                  safety=False), r),
+            "fp32_refine_step_nosafety_ms": _timed(torch, lambda: G.step(dev, node, precision="fp32_refine",
+                                                                         workspace=ws, out=out, safety=False), r),
+            "transport_ms": _timed(torch, lambda: G.transport(tdev, node0, mat, sig, xi, kmax, out=tout), r)}
+        res[key]["fp64_steps_per_s"] = n / (res[key]["fp64_step_ms"] * 1e-3)
+        res[key]["transport_steps_per_s"] = int(tout["steps"].sum().item()) / (res[key]["transport_ms"] * 1e-3)
+    G.set_voxels(True)
+    res["fp64_step_speedup"] = res["brute_force"]["fp64_step_ms"] / res["grids"]["fp64_step_ms"]
+    res["fp64_step_nosafety_speedup"] = (res["brute_force"]["fp64_step_nosafety_ms"] /
+                                         res["grids"]["fp64_step_nosafety_ms"])
+    res["transport_speedup"] = res["brute_force"]["transport_ms"] / res["grids"]["transport_ms"]
     return res
 
 

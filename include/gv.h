@@ -233,6 +233,27 @@ gv_status gv_geom_create(int32_t nnodes, const gv_solid* const* node_solid, cons
                          const double* R, const double* t, gv_geom** out);
 void gv_geom_destroy(gv_geom* g);
 int32_t gv_geom_node_count(const gv_geom* g);
+/* Voxelised navigation (Detector geometry subsection: a volume with many daughters).
+ * gv_geom_create gives every node with at least 16 daughters a uniform grid in the
+ * node's frame over the daughters' bounding boxes (each padded by 1e-6 (1 + |centre|
+ * + half-extent) mm), about one cell per daughter, at most 64 cells per axis; a cell
+ * lists the daughters whose padded box meets it.  With grids on, locate tests only the
+ * daughters listed in the point's cell (a point outside the grid is in none of them),
+ * and a navigation step in such a node walks the cells along the ray in order of
+ * entry (3-D DDA), evaluating DistanceToIn of the listed daughters and stopping once
+ * the best distance so far lies more than 4e-9 (1 + best) mm before the next cell.
+ * SafetyToIn is still taken over every daughter (the step's safety is a minimum over
+ * all of them; pass safety = NULL to leave it out).  Binary64 results (locate, step,
+ * safety, next, transport) are bit-identical with grids on or off: the walk sees every
+ * daughter that could give the minimum or tie with it, and ties are broken by the
+ * same rule.  GV_FP32_REFINE steps walk the grid in binary32 with certified bounds:
+ * next is the same with grids on or off, step and safety within that precision's
+ * tolerance (a track certain on the walk may be refined without it, or the reverse).
+ * enable != 0 turns the grids on (the default), 0 off;
+ * takes effect for launches made after the call.  gv_geom_voxel_count returns the
+ * number of nodes that have a grid. */
+gv_status gv_geom_set_voxels(gv_geom* g, int32_t enable);
+int32_t gv_geom_voxel_count(const gv_geom* g);
 /* node[i] = the deepest node containing point i: start at the world and enter
  * the first daughter (lowest index) that does not classify the point OUTSIDE;
  * -1 if the point is outside the world.  Binary64 decisions. */
@@ -244,7 +265,9 @@ gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* tracks, int32_t* node
  * values of -1 are left out, ties go to the lowest daughter index and a
  * daughter wins over the mother; no candidate -> step = safety = -1.
  * GV_FP32_REFINE needs a workspace of >= tracks->n (a binary32 pass; tracks
- * with an uncertain minimum go to binary64).  Device arrays; async. */
+ * with an uncertain minimum go to binary64).  safety may be NULL: the safeties are
+ * then not evaluated at all (with voxel grids the step no longer scans every
+ * daughter).  Device arrays; async. */
 gv_status gv_nav_step(const gv_geom* g, const gv_tracks* tracks, const int32_t* node, gv_precision prec,
                       double* step, double* safety, int32_t* next, gv_workspace* ws, void* stream);
 

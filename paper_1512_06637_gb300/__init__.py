@@ -268,6 +268,15 @@ class Geometry:
         self.handle = h
         self.nnodes = n
 
+    @property
+    def voxel_count(self) -> int:
+        """Nodes that carry a voxel grid over their daughters."""
+        return int(lib().gv_geom_voxel_count(self.handle))
+
+    def set_voxels(self, enable: bool) -> None:
+        """Use (True, the default) or bypass the daughters' voxel grids."""
+        check(lib().gv_geom_set_voxels(self.handle, 1 if enable else 0))
+
     def locate(self, tracks: dict, out=None, stream=None):
         import torch
         n = tracks["x"].numel()
@@ -278,18 +287,21 @@ class Geometry:
         return out
 
     def step(self, tracks: dict, node, precision: str = "fp64", out: dict | None = None,
-             workspace: Workspace | None = None, stream=None) -> dict:
+             workspace: Workspace | None = None, stream=None, safety: bool = True) -> dict:
+        """One navigation step; ``safety=False`` leaves the safety out (no "safety" entry)."""
         import torch
         n = tracks["x"].numel()
         dev = tracks["x"].device
         if out is None:
             out = {"step": torch.empty(n, dtype=torch.float64, device=dev),
-                   "safety": torch.empty(n, dtype=torch.float64, device=dev),
                    "next": torch.empty(n, dtype=torch.int32, device=dev)}
+            if safety:
+                out["safety"] = torch.empty(n, dtype=torch.float64, device=dev)
         t = tracks_struct(tracks)
         ws = workspace.handle if workspace is not None else None
+        saf = _ptr(out["safety"]) if safety else None
         check(lib().gv_nav_step(self.handle, ctypes.byref(t), _ptr(node), PRECISIONS[precision], _ptr(out["step"]),
-                                _ptr(out["safety"]), _ptr(out["next"]), ws, _stream_ptr(stream)))
+                                saf, _ptr(out["next"]), ws, _stream_ptr(stream)))
         return out
 
     def transport(self, tracks: dict, node0, node_material, sigma_n, xi, kmax: int, out: dict | None = None,

@@ -87,6 +87,8 @@ SIGNATURES = {
     "gv_geom_create": (_i, [ctypes.c_int32, _p, _p, _p, _p, _p]),
     "gv_geom_destroy": (None, [_p]),
     "gv_geom_node_count": (ctypes.c_int32, [_p]),
+    "gv_geom_set_voxels": (_i, [_p, ctypes.c_int32]),
+    "gv_geom_voxel_count": (ctypes.c_int32, [_p]),
     "gv_nav_locate": (_i, [_p, ctypes.POINTER(Tracks), _p, _p]),
     "gv_nav_step": (_i, [_p, ctypes.POINTER(Tracks), _p, _i, _p, _p, _p, _p, _p]),
     "gv_transport": (_i, [_p, ctypes.POINTER(Tracks), _p, _p, _p, ctypes.c_int32, _p, ctypes.c_int32,

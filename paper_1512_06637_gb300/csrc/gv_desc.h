@@ -64,6 +64,7 @@ struct alignas(16) Desc {
   int32_t bpad;
   double bR[9], bt[3];
   const Desc* parts;
+  double ext[3];  // half-extents of an axis-aligned box around the origin holding the solid
 };
 
 // Order-preserving integer key of a binary64 bit pattern: for non-NaN a, b,

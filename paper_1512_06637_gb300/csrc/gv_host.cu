@@ -161,6 +161,8 @@ static gv_status make_trap(const double p[11], int type, gv_solid** out) {
       !face_plane(v[1], v[3], v[7], v[5], cs, h.pl[3]))    // +x
     return set_error(GV_ERR_INVALID_ARG, "trap: a side face is not planar (or is degenerate)");
   h.dz = dz;
+  for (int k = 0; k < 8; k++)
+    for (int i = 0; i < 3; i++) h.ext[i] = std::fmax(h.ext[i], std::fabs(v[k][i]));
   return upload(h, out);
 }
 
@@ -203,6 +205,10 @@ static gv_status make_pcon(int type, int nz, const double* z, const double* rmin
   h.ne[0] = -std::sin(ephi);
   h.ne[1] = std::cos(ephi);
   h.dz = 0.5 * (z[nz - 1] - z[0]);
+  double rm = 0;
+  for (int k = 0; k < nz; k++) rm = std::fmax(rm, rmax[k]);
+  h.ext[0] = h.ext[1] = rm;
+  h.ext[2] = std::fmax(std::fabs(z[0]), std::fabs(z[nz - 1]));
   return upload(h, out);
 }
 
@@ -242,6 +248,7 @@ gv_status gv_solid_box(double dx, double dy, double dz, gv_solid** out) {
   init_desc(h, kBox);
   h.D[0] = dx; h.D[1] = dy; h.D[2] = dz;
   h.dz = dz;
+  h.ext[0] = dx; h.ext[1] = dy; h.ext[2] = dz;
   return upload(h, out);
 }
 
@@ -299,6 +306,11 @@ gv_status gv_solid_boolean(int32_t op, const gv_solid* a, const gv_solid* c, con
   std::memcpy(s->h.bR, R, sizeof(s->h.bR));
   std::memcpy(s->h.bt, t, sizeof(s->h.bt));
   s->h.size = std::fmax(a->h.size, c->h.size);
+  for (int i = 0; i < 3; i++) {  // a's box and the box around c's placed box
+    const double hc = std::fabs(R[3 * i]) * c->h.ext[0] + std::fabs(R[3 * i + 1]) * c->h.ext[1] +
+                      std::fabs(R[3 * i + 2]) * c->h.ext[2];
+    s->h.ext[i] = std::fmax(a->h.ext[i], std::fabs(t[i]) + hc);
+  }
   s->ph[0] = a->h;
   s->ph[1] = c->h;
   s->d = nullptr;

@@ -24,6 +24,7 @@
 #include <cstring>
 #include <new>
 #include <vector>
+#include <array>
 #include "gv_internal.h"
 #include "solid_fp32.cuh"
 #include "solid_fp64.cuh"
@@ -38,7 +39,27 @@ struct alignas(16) NodeD {
   int32_t parent;
   int32_t first;    // daughters: children[first .. first + count)
   int32_t count;
+  int32_t grid;     // voxel grid over the daughters (-1: none)
+  int32_t pad;
 };
+
+// A uniform grid over the daughters of a node, in the node's frame: cell (i, j, k) lists
+// (in increasing node index) the daughters whose bounding box, padded, meets the cell.
+struct GridD {
+  double lo[3], cell[3], inv[3];  // origin, cell edges, their inverses
+  int32_t n[3];                   // cells per axis
+  int32_t start;                  // first cell's entry in the geometry's cell table
+};
+
+// Device pointers of a geometry's grids (grids == nullptr: no grid is used).
+struct Vox {
+  const GridD* grids;
+  const int32_t* cells;  // per cell: [begin, end) into list
+  const int32_t* list;
+};
+
+// Nodes with at least this many daughters get a grid.
+constexpr int kVoxelMin = 16;
 
 constexpr int kLanes = 8;  // lanes per track in the binary32 kernel
 
@@ -50,9 +71,15 @@ struct gv_geom {
   gv::NodeD* d_nodes = nullptr;
   int32_t* d_children = nullptr;
   gv::Desc* d_solids = nullptr;
+  gv::GridD* d_grids = nullptr;
+  int32_t* d_cells = nullptr;
+  int32_t* d_list = nullptr;
+  bool use_vox = true;
   std::vector<gv::NodeD> nodes;
   std::vector<int32_t> children;
   std::vector<gv::Desc> solids;
+  std::vector<gv::GridD> grids;
+  std::vector<int32_t> cells, list;
 };
 
 namespace gv {
@@ -83,8 +110,37 @@ __device__ __forceinline__ void query64(const Desc& S, const f64::Track& T, unsi
   else f64::pcon_query(S, T, want, R);
 }
 
+// The cell of a point given in the grid's node frame; false outside the grid (where no
+// daughter is).
+__device__ __forceinline__ bool grid_cell(const GridD& G, const double q[3], int c[3]) {
+  for (int a = 0; a < 3; a++) {
+    const double f = (q[a] - G.lo[a]) * G.inv[a];
+    if (!(f >= 0.0 && f <= (double)G.n[a])) return false;
+    c[a] = min((int)f, G.n[a] - 1);
+  }
+  return true;
+}
+
+// The daughters of node N to look at for a point (x, y, z) in world coordinates: all of
+// them, or those listed in the point's cell when N has a grid.
+__device__ __forceinline__ void candidates64(const NodeD& N, const int32_t* __restrict__ children, const Vox& vox,
+                                             double x, double y, double z, const int32_t*& ids, int& count) {
+  ids = children + N.first;
+  count = N.count;
+  if (!vox.grids || N.grid < 0) return;
+  const GridD& G = vox.grids[N.grid];
+  double q[3];
+  to_local64(N, x, y, z, q[0], q[1], q[2]);
+  int c[3];
+  if (!grid_cell(G, q, c)) { count = 0; return; }
+  const int cell = G.start + (c[2] * G.n[1] + c[1]) * G.n[0] + c[0];
+  ids = vox.list + vox.cells[2 * cell];
+  count = vox.cells[2 * cell + 1] - vox.cells[2 * cell];
+}
+
 __device__ inline int32_t locate64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                   const Desc* __restrict__ solids, double x, double y, double z) {
+                                   const Desc* __restrict__ solids, double x, double y, double z,
+                                   const Vox& vox = Vox{nullptr, nullptr, nullptr}) {
   f64::Track T{0, 0, 0, 0, 0, 0};
   f64::Result R;
   to_local64(nodes[0], x, y, z, T.x, T.y, T.z);
@@ -94,8 +150,11 @@ __device__ inline int32_t locate64(const NodeD* __restrict__ nodes, const int32_
   for (int depth = 0; depth < 64; depth++) {
     const NodeD& N = nodes[v];
     int32_t into = -1;
-    for (int j = 0; j < N.count; j++) {
-      const int32_t c = children[N.first + j];
+    const int32_t* ids;
+    int count;
+    candidates64(N, children, vox, x, y, z, ids, count);
+    for (int j = 0; j < count; j++) {
+      const int32_t c = ids[j];
       to_local64(nodes[c], x, y, z, T.x, T.y, T.z);
       query64(solids[nodes[c].desc], T, f64::kWantCode, R);
       if (R.code != 2) { into = c; break; }
@@ -109,10 +168,10 @@ __device__ inline int32_t locate64(const NodeD* __restrict__ nodes, const int32_
 __global__ void __launch_bounds__(256, 2) k_locate(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                 const Desc* __restrict__ solids, const double* __restrict__ x,
                                                 const double* __restrict__ y, const double* __restrict__ z,
-                                                int32_t* __restrict__ out, int64_t n) {
+                                                int32_t* __restrict__ out, int64_t n, Vox vox) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    out[i] = locate64(nodes, children, solids, x[i], y[i], z[i]);
+    out[i] = locate64(nodes, children, solids, x[i], y[i], z[i], vox);
 }
 
 struct NavArgs {
@@ -123,52 +182,156 @@ struct NavArgs {
   int64_t n;
 };
 
+// DistanceToIn of the daughters of N (which has a grid) for the ray p + t d (world):
+// the cells the ray crosses are visited in t order and the walk stops once the best
+// candidate so far is before the next cell by more than 4e-9 (1 + best) mm.  Candidates
+// are ranked by (t, node index), the mother (who = -1) after every daughter; runner is the
+// next smaller candidate among those seen (daughters not seen are farther than the margin).
+// A 3-D DDA over the cells of a grid that a ray (node frame) crosses, in order of entry.
+struct Dda {
+  int c[3], step[3];
+  double tnext[3], tdelta[3];
+  double tenter, t1;  // entry of the current cell, exit from the grid
+  int left;           // cells that may still be visited (a ray crosses at most n0 + n1 + n2 - 2)
+  // false: the ray misses the grid
+  __device__ __forceinline__ bool begin(const GridD& G, const double q[3], const double e[3]) {
+    double t0 = 0.0;
+    t1 = CUDART_INF;
+    for (int k = 0; k < 3; k++) {
+      const double lo = G.lo[k], hi = G.lo[k] + G.n[k] * G.cell[k];
+      if (e[k] == 0.0) {
+        if (q[k] < lo || q[k] > hi) return false;
+        continue;
+      }
+      const double ta = (lo - q[k]) / e[k], tb = (hi - q[k]) / e[k];
+      t0 = fmax(t0, fmin(ta, tb));
+      t1 = fmin(t1, fmax(ta, tb));
+    }
+    if (!(t0 <= t1)) return false;
+    for (int k = 0; k < 3; k++) {
+      const double f = (q[k] + t0 * e[k] - G.lo[k]) * G.inv[k];
+      c[k] = min(max((int)floor(f), 0), G.n[k] - 1);
+      if (e[k] > 0) { step[k] = 1; tnext[k] = (G.lo[k] + (c[k] + 1) * G.cell[k] - q[k]) / e[k]; tdelta[k] = G.cell[k] / e[k]; }
+      else if (e[k] < 0) { step[k] = -1; tnext[k] = (G.lo[k] + c[k] * G.cell[k] - q[k]) / e[k]; tdelta[k] = -G.cell[k] / e[k]; }
+      else { step[k] = 0; tnext[k] = CUDART_INF; tdelta[k] = CUDART_INF; }
+    }
+    tenter = t0;
+    left = G.n[0] + G.n[1] + G.n[2] + 3;
+    return true;
+  }
+  __device__ __forceinline__ int cell(const GridD& G) const { return G.start + (c[2] * G.n[1] + c[1]) * G.n[0] + c[0]; }
+  // to the next cell; false once the ray has left the grid
+  __device__ __forceinline__ bool advance(const GridD& G) {
+    int k = 0;
+    if (tnext[1] < tnext[k]) k = 1;
+    if (tnext[2] < tnext[k]) k = 2;
+    tenter = tnext[k];
+    if (!(tenter <= t1) || --left <= 0) return false;
+    c[k] += step[k];
+    if (c[k] < 0 || c[k] >= G.n[k]) return false;
+    tnext[k] += tdelta[k];
+    return true;
+  }
+};
+
+// Stop rule of the walk: no daughter in a cell entered after t can give a distance within
+// the tie margin of `best`.
+__device__ __forceinline__ bool walk_done(double tenter, double best) { return tenter > best + 4e-9 * (1.0 + best); }
+
+__device__ inline void grid_entries(const NodeD* __restrict__ nodes, const Desc* __restrict__ solids, const NodeD& N,
+                                    const Vox& vox, const double p[3], const double d[3], double& best, int32_t& who,
+                                    bool& have, double& runner) {
+  const GridD& G = vox.grids[N.grid];
+  double q[3], e[3];
+  to_local64(N, p[0], p[1], p[2], q[0], q[1], q[2]);
+  rot_local64(N, d[0], d[1], d[2], e[0], e[1], e[2]);
+  Dda D;
+  if (!D.begin(G, q, e)) return;
+  int32_t recent[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  int slot = 0;
+  f64::Track T;
+  f64::Result R;
+  do {
+    if (have && walk_done(D.tenter, best)) break;
+    const int cell = D.cell(G);
+    for (int j = vox.cells[2 * cell]; j < vox.cells[2 * cell + 1]; j++) {
+      const int32_t id = vox.list[j];
+      bool seen = false;
+      for (int r = 0; r < 8; r++) seen |= recent[r] == id;
+      if (seen) continue;
+      recent[slot] = id;
+      slot = (slot + 1) & 7;
+      const NodeD& C = nodes[id];
+      to_local64(C, p[0], p[1], p[2], T.x, T.y, T.z);
+      rot_local64(C, d[0], d[1], d[2], T.u, T.v, T.w);
+      query64(solids[C.desc], T, f64::kWantDin, R);
+      const double t = R.din;
+      if (t >= 0 && (!have || t < best || (t == best && (who == -1 || id < who)))) {
+        if (have && best < runner) runner = best;
+        best = t; who = id; have = true;
+      } else if (t >= 0 && id != who && t < runner) {  // a daughter seen again is not its own runner-up
+        runner = t;
+      }
+    }
+  } while (D.advance(G));
+}
+
 __device__ inline void nav_step64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                  const Desc* __restrict__ solids, int nnodes, const NavArgs& a, int64_t i) {
+                                  const Desc* __restrict__ solids, int nnodes, const NavArgs& a, int64_t i,
+                                  const Vox& vox = Vox{nullptr, nullptr, nullptr}) {
   const int32_t v = a.node[i];
   if (v < 0 || v >= nnodes) {
-    a.step[i] = -1.0; a.safety[i] = -1.0; a.next[i] = -1;
+    a.step[i] = -1.0; a.next[i] = -1;
+    if (a.safety) a.safety[i] = -1.0;
     return;
   }
   const double x = a.x[i], y = a.y[i], z = a.z[i], u = a.u[i], vv = a.v[i], w = a.w[i];
   const NodeD& N = nodes[v];
+  const bool want_saf = a.safety != nullptr;
   f64::Track T;
   f64::Result R;
   to_local64(N, x, y, z, T.x, T.y, T.z);
   rot_local64(N, u, vv, w, T.u, T.v, T.w);
-  query64(solids[N.desc], T, f64::kWantDout | f64::kWantSout, R);
+  query64(solids[N.desc], T, f64::kWantDout | (want_saf ? f64::kWantSout : 0u), R);
   double best = R.dout, saf = R.sout;
-  bool have = best >= 0, have_s = saf >= 0;
+  bool have = best >= 0, have_s = want_saf && saf >= 0;
   int32_t who = -1;
-  for (int j = 0; j < N.count; j++) {
+  const bool grid = vox.grids && N.grid >= 0;
+  const unsigned want = (grid ? 0u : f64::kWantDin) | (want_saf ? f64::kWantSin : 0u);
+  for (int j = 0; want != 0u && j < N.count; j++) {  // with a grid: only the safeties
     const int32_t c = children[N.first + j];
     const NodeD& C = nodes[c];
     to_local64(C, x, y, z, T.x, T.y, T.z);
     rot_local64(C, u, vv, w, T.u, T.v, T.w);
-    query64(solids[C.desc], T, f64::kWantDin | f64::kWantSin, R);
-    if (R.din >= 0 && (!have || R.din < best || (R.din == best && who == -1))) { best = R.din; who = c; have = true; }
-    if (R.sin >= 0 && (!have_s || R.sin < saf)) { saf = R.sin; have_s = true; }
+    query64(solids[C.desc], T, want, R);
+    if (!grid && R.din >= 0 && (!have || R.din < best || (R.din == best && who == -1))) { best = R.din; who = c; have = true; }
+    if (want_saf && R.sin >= 0 && (!have_s || R.sin < saf)) { saf = R.sin; have_s = true; }
+  }
+  if (grid) {
+    const double p[3] = {x, y, z}, dd[3] = {u, vv, w};
+    double runner = CUDART_INF;
+    grid_entries(nodes, solids, N, vox, p, dd, best, who, have, runner);
   }
   a.step[i] = have ? best : -1.0;
-  a.safety[i] = have_s ? saf : -1.0;
+  if (want_saf) a.safety[i] = have_s ? saf : -1.0;
   a.next[i] = have ? who : -1;
 }
 
 __global__ void __launch_bounds__(256) k_nav_fp64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                                  const Desc* __restrict__ solids, int nnodes, NavArgs a) {
+                                                  const Desc* __restrict__ solids, int nnodes, NavArgs a, Vox vox) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
-    nav_step64(nodes, children, solids, nnodes, a, i);
+    nav_step64(nodes, children, solids, nnodes, a, i, vox);
 }
 
 __global__ void __launch_bounds__(256) k_nav_refine(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                     const Desc* __restrict__ solids, int nnodes, NavArgs a,
                                                     const uint32_t* __restrict__ wl,
-                                                    const unsigned long long* __restrict__ cnt) {
+                                                    const unsigned long long* __restrict__ cnt, Vox vox) {
   const int64_t m = (int64_t)*cnt;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
-    nav_step64(nodes, children, solids, nnodes, a, wl[j]);
+    nav_step64(nodes, children, solids, nnodes, a, wl[j], vox);
 }
 
 // ------------------------------------------------------------ binary32
@@ -243,21 +406,38 @@ __device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, uns
 // half of the output tolerance: the certified binary32 results are within it
 __device__ __forceinline__ float half_tol(float t) { return 0.5f * (t < 1e-4f ? 1e-9f : 1e-5f * t); }
 
-// Two smallest candidates (value, error, key); key = daughter order, mother = kMother.
+// Two smallest candidates (value, error, key) of distinct keys; key = daughter order (or
+// node index on a grid walk), mother = kMother.  A key already held is not added again (a
+// daughter met in several cells gives the same value each time).
 struct Top2 {
   float b1, e1, b2, e2;
-  int w1;
+  int w1, w2;
   __device__ __forceinline__ void add(float t, float e, int w) {
-    if (t < b1 || (t == b1 && w < w1)) { b2 = b1; e2 = e1; b1 = t; e1 = e; w1 = w; }
-    else if (t < b2) { b2 = t; e2 = e; }
+    if (w == w1 || w == w2) return;
+    if (t < b1 || (t == b1 && w < w1)) { b2 = b1; e2 = e1; w2 = w1; b1 = t; e1 = e; w1 = w; }
+    else if (t < b2) { b2 = t; e2 = e; w2 = w; }
   }
 };
 
+// Merge the Top2 of the lanes selected by `mask` (a group of kLanes lanes, xor offsets).
+__device__ __forceinline__ void group_merge(unsigned mask, Top2& top) {
+  for (int off = kLanes / 2; off > 0; off >>= 1) {
+    const float ob1 = __shfl_xor_sync(mask, top.b1, off), oe1 = __shfl_xor_sync(mask, top.e1, off);
+    const float ob2 = __shfl_xor_sync(mask, top.b2, off), oe2 = __shfl_xor_sync(mask, top.e2, off);
+    const int ow1 = __shfl_xor_sync(mask, top.w1, off), ow2 = __shfl_xor_sync(mask, top.w2, off);
+    top.add(ob1, oe1, ow1);
+    top.add(ob2, oe2, ow2);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                   const Desc* __restrict__ solids, int nnodes, NavArgs a,
-                                                  uint32_t* __restrict__ wl, unsigned long long* __restrict__ cnt) {
+                                                  uint32_t* __restrict__ wl, unsigned long long* __restrict__ cnt,
+                                                  Vox vox) {
   constexpr int kMother = 0x7ffffffe, kNone = 0x7fffffff;
   const unsigned lane = threadIdx.x & 31u, sub = lane & (kLanes - 1);
+  const unsigned gmask = ((1u << kLanes) - 1u) << (lane & ~(unsigned)(kLanes - 1));
+  const bool want_saf = a.safety != nullptr;
   const int64_t tracks_per_block = blockDim.x / kLanes;
   const int64_t stride = (int64_t)gridDim.x * tracks_per_block;
   const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
@@ -267,9 +447,10 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
     const int64_t i = base + threadIdx.x / kLanes;
     const bool valid = i < a.n;
     bool flag = false;
-    Top2 top{F_INF, 0.f, F_INF, 0.f, kNone};
+    Top2 top{F_INF, 0.f, F_INF, 0.f, kNone, kNone};
     float saf = F_INF;
     int32_t v = -1;
+    bool walked = false;  // keys are node indices (grid walk) rather than daughter order
     if (valid) {
       v = a.node[i];
       if (v < 0 || v >= nnodes) flag = true;
@@ -280,30 +461,53 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
       if (sub == 0) {  // the mother on the group's first lane
         const f32::TrackF L = to_local32(N, W);
         f32::R32 R;
-        query32(solids[N.desc], L, f32::kWantDout | f32::kWantSout, R);
+        query32(solids[N.desc], L, f32::kWantDout | (want_saf ? f32::kWantSout : 0u), R);
         flag |= R.flag || R.dout < 0;  // a point outside its own volume: binary64 decides
         top.add(R.dout, half_tol(R.dout), kMother);
-        saf = R.sout;
+        if (want_saf) saf = R.sout;
       }
-      for (int j = sub; j < N.count; j += kLanes) {
+      walked = vox.grids && N.grid >= 0;
+      const unsigned want = (walked ? 0u : f32::kWantDin) | (want_saf ? f32::kWantSin : 0u);
+      for (int j = sub; want != 0u && j < N.count; j += kLanes) {
         const NodeD& C = nodes[children[N.first + j]];
         const f32::TrackF L = to_local32(C, W);
         f32::R32 R;
-        query32(solids[C.desc], L, f32::kWantDin | f32::kWantSin, R);
+        query32(solids[C.desc], L, want, R);
         flag |= R.flag;
-        if (R.din >= 0) top.add(R.din, half_tol(R.din), j);
-        if (R.sin >= 0) saf = fminf(saf, R.sin);
+        if (!walked && R.din >= 0) top.add(R.din, half_tol(R.din), j);
+        if (want_saf && R.sin >= 0) saf = fminf(saf, R.sin);
+      }
+      if (walked) {  // DistanceToIn of the daughters listed along the ray, cell by cell
+        const GridD& G = vox.grids[N.grid];
+        double q[3], e[3];
+        to_local64(N, a.x[i], a.y[i], a.z[i], q[0], q[1], q[2]);
+        rot_local64(N, a.u[i], a.v[i], a.w[i], e[0], e[1], e[2]);
+        Dda D;
+        if (D.begin(G, q, e)) {
+          do {
+            // every lane of the group holds the group's two best after the merge
+            group_merge(gmask, top);
+            const double bound = (double)top.b1 + (double)top.e1;
+            if (isfinite(top.b1) && walk_done(D.tenter, bound)) break;
+            const int cell = D.cell(G);
+            for (int j = vox.cells[2 * cell] + (int)sub; j < vox.cells[2 * cell + 1]; j += kLanes) {
+              const int32_t id = vox.list[j];
+              const NodeD& C = nodes[id];
+              const f32::TrackF L = to_local32(C, W);
+              f32::R32 R;
+              query32(solids[C.desc], L, f32::kWantDin, R);
+              flag |= R.flag;
+              if (R.din >= 0) top.add(R.din, half_tol(R.din), id);
+            }
+          } while (D.advance(G));
+        }
       }
     }
     // combine the group's lanes with shuffles (xor within the group of kLanes)
+    group_merge(0xffffffffu, top);
     for (int off = kLanes / 2; off > 0; off >>= 1) {
-      const float ob1 = __shfl_xor_sync(0xffffffffu, top.b1, off), oe1 = __shfl_xor_sync(0xffffffffu, top.e1, off);
-      const float ob2 = __shfl_xor_sync(0xffffffffu, top.b2, off), oe2 = __shfl_xor_sync(0xffffffffu, top.e2, off);
-      const int ow1 = __shfl_xor_sync(0xffffffffu, top.w1, off);
       const float os = __shfl_xor_sync(0xffffffffu, saf, off);
       const int of = __shfl_xor_sync(0xffffffffu, (int)flag, off);
-      top.add(ob1, oe1, ow1);
-      top.add(ob2, oe2, kNone);
       saf = fminf(saf, os);
       flag |= of != 0;
     }
@@ -313,8 +517,8 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
     if (valid && sub == 0 && !flag) {
       const NodeD& N = nodes[v];
       a.step[i] = (double)top.b1;
-      a.safety[i] = isfinite(saf) ? (double)saf : -1.0;
-      a.next[i] = top.w1 == kMother ? -1 : children[N.first + top.w1];
+      if (want_saf) a.safety[i] = isfinite(saf) ? (double)saf : -1.0;
+      a.next[i] = top.w1 == kMother ? -1 : walked ? top.w1 : children[N.first + top.w1];
     }
     const bool push = valid && sub == 0 && flag;
     const unsigned m = __ballot_sync(0xffffffffu, push);
@@ -333,7 +537,8 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
 // Locate one point (as locate64) and report whether any classification on the way was
 // SURFACE (the point lies on a boundary within the tolerance).
 __device__ inline int32_t locate64_surf(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                        const Desc* __restrict__ solids, double x, double y, double z, bool& surf) {
+                                        const Desc* __restrict__ solids, double x, double y, double z, bool& surf,
+                                        const Vox& vox) {
   f64::Track T{0, 0, 0, 0, 0, 0};
   f64::Result R;
   to_local64(nodes[0], x, y, z, T.x, T.y, T.z);
@@ -344,8 +549,11 @@ __device__ inline int32_t locate64_surf(const NodeD* __restrict__ nodes, const i
   for (int depth = 0; depth < 64; depth++) {
     const NodeD& N = nodes[v];
     int32_t into = -1;
-    for (int j = 0; j < N.count; j++) {
-      const int32_t c = children[N.first + j];
+    const int32_t* ids;
+    int count;
+    candidates64(N, children, vox, x, y, z, ids, count);  // a daughter whose band holds the point is listed
+    for (int j = 0; j < count; j++) {
+      const int32_t c = ids[j];
       to_local64(nodes[c], x, y, z, T.x, T.y, T.z);
       query64(solids[nodes[c].desc], T, f64::kWantCode, R);
       surf |= R.code == 1;
@@ -361,7 +569,7 @@ __device__ inline int32_t locate64_surf(const NodeD* __restrict__ nodes, const i
 // safety), and the next smaller candidate distance.
 __device__ inline void nav_one64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                  const Desc* __restrict__ solids, int32_t v, const double p[3], const double d[3],
-                                 double& step, int32_t& next, double& second) {
+                                 double& step, int32_t& next, double& second, const Vox& vox) {
   const NodeD& N = nodes[v];
   f64::Track T;
   f64::Result R;
@@ -371,6 +579,13 @@ __device__ inline void nav_one64(const NodeD* __restrict__ nodes, const int32_t*
   double best = R.dout, runner = CUDART_INF;
   bool have = best >= 0;
   int32_t who = -1;
+  if (vox.grids && N.grid >= 0) {
+    grid_entries(nodes, solids, N, vox, p, d, best, who, have, runner);
+    step = have ? best : -1.0;
+    next = have ? who : -1;
+    second = runner;
+    return;
+  }
   for (int j = 0; j < N.count; j++) {
     const int32_t c = children[N.first + j];
     const NodeD& C = nodes[c];
@@ -429,11 +644,12 @@ __device__ __forceinline__ void flight_begin(const TransportArgs& a, int64_t i, 
 
 // One step of the loop of the Physics subsection (see gv.h) for track i.
 __device__ inline void flight_step(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                   const Desc* __restrict__ solids, const TransportArgs& a, int64_t i, Flight& F) {
+                                   const Desc* __restrict__ solids, const TransportArgs& a, int64_t i, Flight& F,
+                                   const Vox& vox) {
   const double* r = a.xi + ((size_t)i * (size_t)a.kmax + (size_t)F.k) * 4;
   double dgeo, second;
   int32_t next;
-  nav_one64(nodes, children, solids, F.v, F.p, F.d, dgeo, next, second);
+  nav_one64(nodes, children, solids, F.v, F.p, F.d, dgeo, next, second, vox);
   const int32_t m = a.material[F.v];
   if (dgeo < 0 || m < 0 || m >= a.nmat) { F.why = GV_LOST; F.live = false; return; }
   const double sig0 = a.sigma_n[2 * m], sig1 = a.sigma_n[2 * m + 1];
@@ -458,7 +674,7 @@ __device__ inline void flight_step(const NodeD* __restrict__ nodes, const int32_
     F.len = xadd(F.len, dgeo);
     bool surf = false;
     F.v = locate64_surf(nodes, children, solids, xadd(F.p[0], xmul(kPush, F.d[0])),
-                        xadd(F.p[1], xmul(kPush, F.d[1])), xadd(F.p[2], xmul(kPush, F.d[2])), surf);
+                        xadd(F.p[1], xmul(kPush, F.d[1])), xadd(F.p[2], xmul(kPush, F.d[2])), surf, vox);
     F.near |= surf;
     if (F.v < 0) { F.why = GV_ESCAPED; F.live = false; return; }
   }
@@ -478,7 +694,7 @@ __device__ __forceinline__ void flight_end(const TransportArgs& a, int64_t i, co
 // contiguous range of tracks and keeps one in each lane; when at least half its lanes are
 // idle they take the next tracks of the range, then every busy lane takes one step.
 __global__ void __launch_bounds__(256) k_transport(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                                   const Desc* __restrict__ solids, TransportArgs a) {
+                                                   const Desc* __restrict__ solids, TransportArgs a, Vox vox) {
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
   const int64_t warp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int64_t chunk = (a.n + nwarps - 1) / nwarps;
@@ -505,7 +721,7 @@ __global__ void __launch_bounds__(256) k_transport(const NodeD* __restrict__ nod
       continue;
     }
     if (busy) {
-      flight_step(nodes, children, solids, a, i, F);
+      flight_step(nodes, children, solids, a, i, F, vox);
       if (!F.live) {
         flight_end(a, i, F);
         busy = false;
@@ -522,6 +738,76 @@ static void split_f(double v, float& h, float& l) {
   h = (float)v;
   l = (float)(v - (double)h);
 }
+
+namespace gv {
+
+// Half-extents of an origin-centred box holding the solid in its own frame, recorded by
+// the solid's constructor.
+static void solid_half(const Desc& h, double e[3]) {
+  for (int i = 0; i < 3; i++) e[i] = h.ext[i];
+}
+
+// Grids for the nodes with at least kVoxelMin daughters: the box around the daughters'
+// (padded) bounding boxes in the node's frame, cut into about one cell per daughter.
+static void build_grids(gv_geom* g) {
+  for (int v = 0; v < g->nnodes; v++) {
+    NodeD& N = g->nodes[v];
+    N.grid = -1;
+    if (N.count < kVoxelMin) continue;
+    std::vector<std::array<double, 6>> box(N.count);  // lo, hi per daughter in v's frame
+    double glo[3] = {1e300, 1e300, 1e300}, ghi[3] = {-1e300, -1e300, -1e300};
+    for (int j = 0; j < N.count; j++) {
+      const NodeD& C = g->nodes[g->children[N.first + j]];
+      // p_v = Rv^T (Rc p_c + tc - tv): M = Rv^T Rc, b = Rv^T (tc - tv)
+      double M[9], b[3], e[3];
+      for (int r = 0; r < 3; r++) {
+        for (int c = 0; c < 3; c++)
+          M[3 * r + c] = N.R[0 * 3 + r] * C.R[0 * 3 + c] + N.R[1 * 3 + r] * C.R[1 * 3 + c] + N.R[2 * 3 + r] * C.R[2 * 3 + c];
+        b[r] = N.R[0 * 3 + r] * (C.t[0] - N.t[0]) + N.R[1 * 3 + r] * (C.t[1] - N.t[1]) + N.R[2 * 3 + r] * (C.t[2] - N.t[2]);
+      }
+      solid_half(g->solids[C.desc], e);
+      for (int r = 0; r < 3; r++) {
+        const double h = std::fabs(M[3 * r]) * e[0] + std::fabs(M[3 * r + 1]) * e[1] + std::fabs(M[3 * r + 2]) * e[2];
+        const double pad = 1e-6 * (1.0 + std::fabs(b[r]) + h);  // far above the rounding of any frame change
+        box[j][r] = b[r] - h - pad;
+        box[j][3 + r] = b[r] + h + pad;
+        glo[r] = std::fmin(glo[r], box[j][r]);
+        ghi[r] = std::fmax(ghi[r], box[j][3 + r]);
+      }
+    }
+    GridD G;
+    const double vol = std::fmax((ghi[0] - glo[0]) * (ghi[1] - glo[1]) * (ghi[2] - glo[2]), 1e-300);
+    const double edge = std::cbrt(vol / N.count);
+    for (int r = 0; r < 3; r++) {
+      G.n[r] = (int)std::min(64.0, std::max(1.0, std::ceil((ghi[r] - glo[r]) / edge)));
+      G.lo[r] = glo[r];
+      G.cell[r] = (ghi[r] - glo[r]) / G.n[r];
+      G.inv[r] = 1.0 / G.cell[r];
+    }
+    G.start = (int)(g->cells.size() / 2);
+    const int ncell = G.n[0] * G.n[1] * G.n[2];
+    std::vector<std::vector<int32_t>> lists(ncell);
+    for (int j = 0; j < N.count; j++) {  // daughters in increasing node index
+      int c0[3], c1[3];
+      for (int r = 0; r < 3; r++) {
+        c0[r] = std::max(0, std::min(G.n[r] - 1, (int)std::floor((box[j][r] - G.lo[r]) * G.inv[r])));
+        c1[r] = std::max(0, std::min(G.n[r] - 1, (int)std::floor((box[j][3 + r] - G.lo[r]) * G.inv[r])));
+      }
+      for (int k = c0[2]; k <= c1[2]; k++)
+        for (int jj = c0[1]; jj <= c1[1]; jj++)
+          for (int i = c0[0]; i <= c1[0]; i++) lists[(k * G.n[1] + jj) * G.n[0] + i].push_back(g->children[N.first + j]);
+    }
+    for (int q = 0; q < ncell; q++) {
+      g->cells.push_back((int32_t)g->list.size());
+      g->list.insert(g->list.end(), lists[q].begin(), lists[q].end());
+      g->cells.push_back((int32_t)g->list.size());
+    }
+    N.grid = (int)g->grids.size();
+    g->grids.push_back(G);
+  }
+}
+
+}  // namespace gv
 
 extern "C" {
 
@@ -579,6 +865,8 @@ gv_status gv_geom_create(int32_t nnodes, const gv_solid* const* node_solid, cons
   }
   g->nsolids = (int)uniq.size();
   const int nrec = table_size(uniq.data(), g->nsolids);  // booleans carry their components along
+  for (const gv_solid* u : uniq) g->solids.push_back(u->h);  // host copies for the grid builder
+  build_grids(g);
   cudaError_t e = cudaGetDevice(&g->device);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_nodes, sizeof(NodeD) * nnodes);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_children, sizeof(int32_t) * g->children.size());
@@ -588,6 +876,15 @@ gv_status gv_geom_create(int32_t nnodes, const gv_solid* const* node_solid, cons
   if (e == cudaSuccess)
     e = cudaMemcpy(g->d_children, g->children.data(), sizeof(int32_t) * g->children.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_solids, g->solids.data(), sizeof(Desc) * nrec, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !g->grids.empty()) {
+    e = cudaMalloc(&g->d_grids, sizeof(GridD) * g->grids.size());
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_cells, sizeof(int32_t) * g->cells.size());
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_list, sizeof(int32_t) * std::max<size_t>(g->list.size(), 1));
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_grids, g->grids.data(), sizeof(GridD) * g->grids.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_cells, g->cells.data(), sizeof(int32_t) * g->cells.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !g->list.empty())
+      e = cudaMemcpy(g->d_list, g->list.data(), sizeof(int32_t) * g->list.size(), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     gv_geom_destroy(g);
     return e == cudaErrorMemoryAllocation ? set_error(GV_ERR_OUT_OF_MEMORY, "geom: cudaMalloc failed") : cuda_error(e, "geom upload");
@@ -601,10 +898,26 @@ void gv_geom_destroy(gv_geom* g) {
   if (g->d_nodes) cudaFree(g->d_nodes);
   if (g->d_children) cudaFree(g->d_children);
   if (g->d_solids) cudaFree(g->d_solids);
+  if (g->d_grids) cudaFree(g->d_grids);
+  if (g->d_cells) cudaFree(g->d_cells);
+  if (g->d_list) cudaFree(g->d_list);
   delete g;
 }
 
+gv_status gv_geom_set_voxels(gv_geom* g, int32_t enable) {
+  if (!g) return set_error(GV_ERR_INVALID_ARG, "geom: NULL geometry");
+  g->use_vox = enable != 0;
+  return GV_OK;
+}
+
+int32_t gv_geom_voxel_count(const gv_geom* g) { return g ? (int32_t)g->grids.size() : 0; }
+
 int32_t gv_geom_node_count(const gv_geom* g) { return g ? g->nnodes : 0; }
+
+static gv::Vox vox_of(const gv_geom* g) {
+  if (!g->use_vox || !g->d_grids) return gv::Vox{nullptr, nullptr, nullptr};
+  return gv::Vox{g->d_grids, g->d_cells, g->d_list};
+}
 
 gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* t, int32_t* node, void* stream) {
   if (!g || !t) return set_error(GV_ERR_INVALID_ARG, "locate: NULL geometry or tracks");
@@ -613,7 +926,7 @@ gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* t, int32_t* node, voi
   if (!t->x || !t->y || !t->z || !node) return set_error(GV_ERR_INVALID_ARG, "locate: NULL array");
   int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sm_count() * 8);
   k_locate<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, t->x, t->y,
-                                                                 t->z, node, t->n);
+                                                                 t->z, node, t->n, vox_of(g));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GV_OK : cuda_error(e, "locate launch");
 }
@@ -624,9 +937,9 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
   if (prec != GV_FP64 && prec != GV_FP32_REFINE) return set_error(GV_ERR_INVALID_ARG, "unknown precision");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "nav: negative track count");
   if (t->n == 0) return GV_OK;
-  if (!t->x || !t->y || !t->z || !t->dx || !t->dy || !t->dz || !node || !step || !safety || !next)
+  if (!t->x || !t->y || !t->z || !t->dx || !t->dy || !t->dz || !node || !step || !next)
     return set_error(GV_ERR_INVALID_ARG, "nav: NULL array");
-  const void* ptrs[8] = {t->x, t->y, t->z, t->dx, t->dy, t->dz, step, safety};
+  const void* ptrs[8] = {t->x, t->y, t->z, t->dx, t->dy, t->dz, step, safety};  // safety may be NULL
   for (int i = 0; i < 8; i++)
     if ((uintptr_t)ptrs[i] & 7u) return set_error(GV_ERR_INVALID_ARG, "nav: arrays must be 8-byte aligned");
   NavArgs a{t->x, t->y, t->z, t->dx, t->dy, t->dz, node, step, safety, next, t->n};
@@ -634,7 +947,7 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
   const int sms = sm_count();
   if (prec == GV_FP64) {
     int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sms * 8);
-    k_nav_fp64<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a);
+    k_nav_fp64<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, vox_of(g));
   } else {
     if (!ws) return set_error(GV_ERR_INVALID_ARG, "nav: GV_FP32_REFINE needs a workspace");
     if (ws->cap < t->n) return set_error(GV_ERR_OUT_OF_MEMORY, "nav: workspace smaller than the basket");
@@ -643,9 +956,9 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
     const int64_t per_block = 256 / kLanes;
     int64_t blocks = std::min<int64_t>((t->n + per_block - 1) / per_block, (int64_t)sms * 8);
     k_nav_fp32<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, ws->idx,
-                                                  ws->counter);
+                                                  ws->counter, vox_of(g));
     k_nav_refine<<<(unsigned)(sms * 2), 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, ws->idx,
-                                                       ws->counter);
+                                                       ws->counter, vox_of(g));
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GV_OK : cuda_error(e, "nav launch");
@@ -669,7 +982,7 @@ gv_status gv_transport(const gv_geom* g, const gv_tracks* t, const int32_t* node
                   out->reason, out->steps, out->x, out->y, out->z, out->path, out->last, out->tie, t->n};
   const int sms = sm_count();
   const int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sms * 8);
-  k_transport<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, a);
+  k_transport<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, a, vox_of(g));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GV_OK : cuda_error(e, "transport launch");
 }

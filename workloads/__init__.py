@@ -408,6 +408,101 @@ def nested_tracks(n: int, seed: int, geom: dict | None = None) -> dict:
     return soa(pts, isotropic(n, g))
 
 
+def _scaled(spec: dict, f: float) -> dict:
+    """A primitive solid with every length multiplied by f (angles kept)."""
+    kind, p = spec["kind"], spec["params"]
+    if kind in ("box", "trd"):
+        return {"kind": kind, "params": tuple(f * v for v in p)}
+    if kind == "trap":
+        q = list(p[0])
+        for i in (0, 3, 4, 5, 7, 8, 9):
+            q[i] *= f
+        return {"kind": kind, "params": (tuple(q),)}
+    if kind == "tube":
+        return {"kind": kind, "params": (f * p[0], f * p[1], f * p[2], p[3], p[4])}
+    if kind == "cone":
+        return {"kind": kind, "params": tuple(f * v for v in p[:5]) + (p[5], p[6])}
+    z, rmin, rmax, sphi, dphi = p
+    return {"kind": kind, "params": (tuple(f * v for v in z), tuple(f * v for v in rmin),
+                                     tuple(f * v for v in rmax), sphi, dphi)}
+
+
+def crowded_geometry(lattice: int = 12, seed: int = 0) -> dict:
+    """A volume with many daughters: world box (600, 600, 600) mm holding a lattice^3 array of
+    daughters at a 100 mm pitch (1728 by default), each a random solid of the six kinds or
+    a boolean (every eighth), randomly rotated about its lattice point and shifted by up to
+    5 mm, its bounding sphere under 45 mm so that neighbours do not overlap.  The daughter
+    at lattice point (0, 0, 0) is instead a box (28, 28, 28), rotated, that holds a 3 x 3 x 3
+    array of small solids at an 18 mm pitch, bounding spheres under 9 mm (27 daughters, a
+    second level with its own grid)."""
+    g = rng(8000 + seed)
+    solids = [{"kind": "box", "params": (600.0, 600.0, 600.0)}]
+    table = []
+    while len(table) < 40:
+        k = len(table)
+        spec = boolean_random(g, lo=5.0, hi=18.0) if k % 8 == 7 else random_solid(KINDS6[k % 6], g, lo=4.0, hi=26.0)
+        if np.linalg.norm(bounding_half(spec)) < 45.0:
+            table.append(spec)
+    small = []
+    while len(small) < 12:
+        spec = _scaled(random_solid(KINDS6[len(small) % 6], g, lo=4.0, hi=26.0), 0.2)
+        if np.linalg.norm(bounding_half(spec)) < 9.0:
+            small.append(spec)
+    solids += table + small + [{"kind": "box", "params": (28.0, 28.0, 28.0)}]
+    first_small, sub_box = 1 + len(table), len(solids) - 1
+    nodes = [{"solid": 0, "parent": -1, "R": np.eye(3), "t": np.zeros(3)}]
+    c0 = -0.5 * (lattice - 1) * 100.0
+    sub = -1
+    for i in range(lattice):
+        for j in range(lattice):
+            for k in range(lattice):
+                t = np.array([c0 + 100.0 * i, c0 + 100.0 * j, c0 + 100.0 * k])
+                if i == j == k == 0:
+                    sub = len(nodes)
+                    nodes.append({"solid": sub_box, "parent": 0, "R": random_rotation(g), "t": t})
+                else:
+                    nodes.append({"solid": 1 + int(g.integers(len(table))), "parent": 0, "R": random_rotation(g),
+                                  "t": t + g.uniform(-5, 5, 3)})
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                nodes.append({"solid": first_small + int(g.integers(len(small))), "parent": sub,
+                              "R": random_rotation(g), "t": np.array([18.0 * (i - 1), 18.0 * (j - 1), 18.0 * (k - 1)])})
+    return {"solids": solids, "nodes": nodes}
+
+
+def crowded_tracks(geom: dict, n: int, seed: int, surf_frac: float = 0.3, axis_frac: float = 0.1) -> dict:
+    """Points for a crowded geometry: uniform in the world box, except a fraction drawn on the
+    surfaces of random daughters of the world (placed in world coordinates); isotropic
+    directions, except a fraction along +-x, +-y or +-z (rays parallel to grid planes)."""
+    g = rng(9000 + seed)
+    hb = np.array(geom["solids"][0]["params"])
+    pts = g.uniform(-1, 1, (n, 3)) * hb
+    d = isotropic(n, g)
+    m = int(n * surf_frac)
+    kids = [i for i, nd in enumerate(geom["nodes"]) if nd["parent"] == 0]
+    pick = g.choice(kids, m)
+    for v in np.unique(pick):
+        sel = np.nonzero(pick == v)[0]
+        nd = geom["nodes"][v]
+        loc = _sample_surface(geom["solids"][nd["solid"]], len(sel), g)
+        pts[sel] = loc @ np.asarray(nd["R"]).T + nd["t"]
+    a = int(n * axis_frac)
+    idx = g.choice(n, a, replace=False)
+    ax = g.integers(0, 3, a)
+    d[idx] = 0.0
+    d[idx, ax] = np.where(g.random(a) < 0.5, -1.0, 1.0)
+    perm = g.permutation(n)
+    return soa(pts[perm], d)
+
+
+def crowded_materials(geom: dict) -> dict:
+    """Materials for the transport loop in a crowded geometry: the world a light material
+    (mean free paths 400 / 2000 mm), the daughters a dense one (20 / 80 mm)."""
+    mat = np.array([0 if nd["parent"] < 0 else 1 for nd in geom["nodes"]], np.int32)
+    return {"node_material": mat, "sigma_n": np.array([[0.0025, 0.0005], [0.05, 0.0125]])}
+
+
 def transport_materials(geom: dict) -> dict:
     """Materials of the nested detector for the transport loop: the world is vacuum, the tube
     shells a light material, the box cells a dense one; n sigma of (scatter, absorb) in 1/mm
