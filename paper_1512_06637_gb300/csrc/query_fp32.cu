@@ -19,8 +19,14 @@ __device__ __forceinline__ void stage_desc32(Desc& dst, const Desc* __restrict__
   for (int i = threadIdx.x; i < (int)(sizeof(Desc) / 16); i += blockDim.x) d[i] = s[i];
 }
 
+// Block shape of the one-track-per-thread pass per family (box, trd/trap, tube, cone):
+// threads and resident blocks per SM, from the registers each family needs.
+template <int FAMILY> struct Shape32 { static constexpr int threads = 256, blocks = 3; };
+template <> struct Shape32<0> { static constexpr int threads = 288, blocks = 4; };
+template <> struct Shape32<1> { static constexpr int threads = 288, blocks = 3; };
+
 template <int FAMILY>
-__global__ void __launch_bounds__(256, FAMILY == 0 ? 4 : (FAMILY == 1 ? 2 : 3)) k_query_fp32(const Desc* __restrict__ desc, QueryArgs a,
+__global__ void __launch_bounds__(Shape32<FAMILY>::threads, Shape32<FAMILY>::blocks) k_query_fp32(const Desc* __restrict__ desc, QueryArgs a,
                                                     uint32_t* __restrict__ worklist,
                                                     unsigned long long* __restrict__ counter) {
   __shared__ Desc S;
@@ -97,9 +103,11 @@ constexpr int kRefillIdle = 16;
 // tube and one-section cones: the walk is one or two sections long, so the plain kernel
 // (one track per thread, no refill) is used for them
 constexpr bool kWalkOneSection = false;
+// threads per block of the walk kernel (two blocks per SM: the register budget sets it)
+constexpr int kWalkThreads = 320;
 
 template <int FAMILY>
-__global__ void __launch_bounds__(256, 2) k_query_walk(const Desc* __restrict__ desc, QueryArgs a,
+__global__ void __launch_bounds__(kWalkThreads, 2) k_query_walk(const Desc* __restrict__ desc, QueryArgs a,
                                                       uint32_t* __restrict__ worklist,
                                                       unsigned long long* __restrict__ counter) {
   __shared__ Desc S;
@@ -186,6 +194,17 @@ __global__ void __launch_bounds__(256) k_refine_fp64(const Desc* __restrict__ de
   }
 }
 
+// The binary32 pass of one family: a grid of at most eight blocks' worth of tracks per SM
+// (grid-stride loop inside).
+template <int FAMILY>
+void launch_pass32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist, unsigned long long* counter,
+                   cudaStream_t stream, int sms) {
+  constexpr int T = Shape32<FAMILY>::threads;
+  int64_t blocks = (a.n + T - 1) / T;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  k_query_fp32<FAMILY><<<(unsigned)blocks, T, 0, stream>>>(s->d, a, worklist, counter);
+}
+
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,
                               unsigned long long* counter, cudaStream_t stream) {
   // counter[0]: worklist length; counter[1]: next track of the lane-refill dispenser
@@ -204,26 +223,26 @@ cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* w
   const unsigned rblocks = (unsigned)(blocks < (int64_t)sms * 2 ? blocks : (int64_t)sms * 2);
   switch (s->h.type) {
     case kBox:
-      k_query_fp32<0><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+      launch_pass32<0>(s, a, worklist, counter, stream, sms);
       k_refine_fp64<0><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
     case kTrd:
     case kTrap:
-      k_query_fp32<1><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+      launch_pass32<1>(s, a, worklist, counter, stream, sms);
       k_refine_fp64<1><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
     case kTube:
       if (kWalkOneSection)
-        k_query_walk<2><<<wblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+        k_query_walk<2><<<wblocks, kWalkThreads, 0, stream>>>(s->d, a, worklist, counter);
       else
-        k_query_fp32<2><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+        launch_pass32<2>(s, a, worklist, counter, stream, sms);
       k_refine_fp64<2><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
     default:
       if (s->h.nz > 2 || kWalkOneSection)
-        k_query_walk<3><<<wblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+        k_query_walk<3><<<wblocks, kWalkThreads, 0, stream>>>(s->d, a, worklist, counter);
       else
-        k_query_fp32<3><<<(unsigned)blocks, threads, 0, stream>>>(s->d, a, worklist, counter);
+        launch_pass32<3>(s, a, worklist, counter, stream, sms);
       k_refine_fp64<2><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
   }
