@@ -39,8 +39,8 @@ BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 double
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass); valid only while the kernel
 # sources hash to the value recorded with them, else the bench reports traffic = null.
 DRAM_CAPTURE = {
-    "sources_sha256": "2e15495c9a6de4f0f5dbaef9bd873a46998d0f31bd07300924f43d3a9b2c86fa",
-    "bytes_per_track": {'box': 79.07, 'trd': 78.96, 'tube': 79.26, 'cone': 79.44, 'polycone': 79.81},
+    "sources_sha256": "4475fae554066ad2992e6e8b0e8b1559d80fd6fe652d71d3f75b28f8f22b05ba",
+    "bytes_per_track": {'box': 79.00, 'trd': 78.97, 'tube': 79.28, 'cone': 79.42, 'polycone': 80.37},
     "profile": "profiles/query_fp32_dram_full.md",
 }
 KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")

@@ -246,7 +246,8 @@ int32_t gv_geom_node_count(const gv_geom* g);
  * all of them; pass safety = NULL to leave it out).  Binary64 results (locate, step,
  * safety, next, transport) are bit-identical with grids on or off: the walk sees every
  * daughter that could give the minimum or tie with it, and ties are broken by the
- * same rule.  GV_FP32_REFINE steps walk the grid in binary32 with certified bounds:
+ * same rule.  GV_FP32_REFINE steps in a node with at least 128 daughters walk the
+ * grid in binary32 with certified bounds (below that, 8 lanes per track scan them all):
  * next is the same with grids on or off, step and safety within that precision's
  * tolerance (a track certain on the walk may be refined without it, or the reverse).
  * enable != 0 turns the grids on (the default), 0 off;

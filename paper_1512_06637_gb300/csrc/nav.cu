@@ -60,6 +60,10 @@ struct Vox {
 
 // Nodes with at least this many daughters get a grid.
 constexpr int kVoxelMin = 16;
+// The binary32 pass walks a node's grid only from this many daughters on: its walk (a
+// binary64 DDA per lane, a group merge per cell) costs more than 8 lanes scanning a few
+// dozen daughters.
+constexpr int kWalk32Min = 128;
 
 constexpr int kLanes = 8;  // lanes per track in the binary32 kernel
 
@@ -75,6 +79,7 @@ struct gv_geom {
   int32_t* d_cells = nullptr;
   int32_t* d_list = nullptr;
   bool use_vox = true;
+  bool walk32 = false;  // some node with a grid has at least kWalk32Min daughters
   std::vector<gv::NodeD> nodes;
   std::vector<int32_t> children;
   std::vector<gv::Desc> solids;
@@ -406,30 +411,43 @@ __device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, uns
 // half of the output tolerance: the certified binary32 results are within it
 __device__ __forceinline__ float half_tol(float t) { return 0.5f * (t < 1e-4f ? 1e-9f : 1e-5f * t); }
 
-// Two smallest candidates (value, error, key) of distinct keys; key = daughter order (or
-// node index on a grid walk), mother = kMother.  A key already held is not added again (a
-// daughter met in several cells gives the same value each time).
+// Two smallest candidates (value, error, key); key = daughter order (or node index on a
+// grid walk), mother = kMother.  With DEDUP the two keys are distinct: a key already held
+// is not added again (a daughter met in several cells gives the same value each time);
+// without it (every daughter evaluated once) the second key is not tracked.
+template <bool DEDUP>
 struct Top2 {
   float b1, e1, b2, e2;
   int w1, w2;
   __device__ __forceinline__ void add(float t, float e, int w) {
-    if (w == w1 || w == w2) return;
-    if (t < b1 || (t == b1 && w < w1)) { b2 = b1; e2 = e1; w2 = w1; b1 = t; e1 = e; w1 = w; }
-    else if (t < b2) { b2 = t; e2 = e; w2 = w; }
+    if (DEDUP && (w == w1 || w == w2)) return;
+    if (t < b1 || (t == b1 && w < w1)) {
+      if (DEDUP) w2 = w1;
+      b2 = b1; e2 = e1; b1 = t; e1 = e; w1 = w;
+    } else if (t < b2) {
+      b2 = t; e2 = e;
+      if (DEDUP) w2 = w;
+    }
   }
 };
 
 // Merge the Top2 of the lanes selected by `mask` (a group of kLanes lanes, xor offsets).
-__device__ __forceinline__ void group_merge(unsigned mask, Top2& top) {
+template <bool DEDUP>
+__device__ __forceinline__ void group_merge(unsigned mask, Top2<DEDUP>& top) {
+  constexpr int kNone = 0x7fffffff;
   for (int off = kLanes / 2; off > 0; off >>= 1) {
     const float ob1 = __shfl_xor_sync(mask, top.b1, off), oe1 = __shfl_xor_sync(mask, top.e1, off);
     const float ob2 = __shfl_xor_sync(mask, top.b2, off), oe2 = __shfl_xor_sync(mask, top.e2, off);
-    const int ow1 = __shfl_xor_sync(mask, top.w1, off), ow2 = __shfl_xor_sync(mask, top.w2, off);
+    const int ow1 = __shfl_xor_sync(mask, top.w1, off);
+    const int ow2 = DEDUP ? __shfl_xor_sync(mask, top.w2, off) : kNone;
     top.add(ob1, oe1, ow1);
     top.add(ob2, oe2, ow2);
   }
 }
 
+// WALK: the geometry has nodes whose daughters the pass finds by walking their grid (the
+// instance without it keeps the registers of the plain scan).
+template <bool WALK>
 __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                   const Desc* __restrict__ solids, int nnodes, NavArgs a,
                                                   uint32_t* __restrict__ wl, unsigned long long* __restrict__ cnt,
@@ -447,7 +465,7 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
     const int64_t i = base + threadIdx.x / kLanes;
     const bool valid = i < a.n;
     bool flag = false;
-    Top2 top{F_INF, 0.f, F_INF, 0.f, kNone, kNone};
+    Top2<WALK> top{F_INF, 0.f, F_INF, 0.f, kNone, kNone};
     float saf = F_INF;
     int32_t v = -1;
     bool walked = false;  // keys are node indices (grid walk) rather than daughter order
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
         top.add(R.dout, half_tol(R.dout), kMother);
         if (want_saf) saf = R.sout;
       }
-      walked = vox.grids && N.grid >= 0;
+      walked = WALK && vox.grids && N.grid >= 0 && N.count >= kWalk32Min;
       const unsigned want = (walked ? 0u : f32::kWantDin) | (want_saf ? f32::kWantSin : 0u);
       for (int j = sub; want != 0u && j < N.count; j += kLanes) {
         const NodeD& C = nodes[children[N.first + j]];
@@ -477,7 +495,7 @@ __global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ node
         if (!walked && R.din >= 0) top.add(R.din, half_tol(R.din), j);
         if (want_saf && R.sin >= 0) saf = fminf(saf, R.sin);
       }
-      if (walked) {  // DistanceToIn of the daughters listed along the ray, cell by cell
+      if (WALK && walked) {  // DistanceToIn of the daughters listed along the ray, cell by cell
         const GridD& G = vox.grids[N.grid];
         double q[3], e[3];
         to_local64(N, a.x[i], a.y[i], a.z[i], q[0], q[1], q[2]);
@@ -804,6 +822,7 @@ static void build_grids(gv_geom* g) {
     }
     N.grid = (int)g->grids.size();
     g->grids.push_back(G);
+    if (N.count >= kWalk32Min) g->walk32 = true;
   }
 }
 
@@ -955,8 +974,13 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
     if (e != cudaSuccess) return cuda_error(e, "nav: counter reset");
     const int64_t per_block = 256 / kLanes;
     int64_t blocks = std::min<int64_t>((t->n + per_block - 1) / per_block, (int64_t)sms * 8);
-    k_nav_fp32<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, ws->idx,
-                                                  ws->counter, vox_of(g));
+    const Vox vox = vox_of(g);
+    if (vox.grids && g->walk32)
+      k_nav_fp32<true><<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a,
+                                                         ws->idx, ws->counter, vox);
+    else
+      k_nav_fp32<false><<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a,
+                                                          ws->idx, ws->counter, vox);
     k_nav_refine<<<(unsigned)(sms * 2), 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, ws->idx,
                                                        ws->counter, vox_of(g));
   }
