@@ -142,6 +142,44 @@ def cpu_baseline(tracks_per_solid: dict, sample: int):
             "sample": f"first {sample} tracks of each of the 5 solids' 2^24-track baskets, all five queries"}
 
 
+def cpu_baseline_extras():
+    """The oracle beside the other forms, all host cores, on bounded samples of their
+    workloads: the transport loop (nested detector, 16384 tracks, kmax 64), boolean solids
+    (the bench's three, 100000 tracks each, all five queries), the navigation step in the
+    nested detector (100000 tracks) and in the crowded lattice (20000 tracks, every daughter
+    scanned)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    res = {"cores": threads}
+    geo = W.nested_geometry()
+    O = oracle.Geometry(geo["solids"], geo["nodes"])
+    n, kmax = 16384, 64
+    tr = W.nested_tracks(n, seed=11, geom=geo)
+    node0 = O.locate(tr["x"], tr["y"], tr["z"], threads=threads)
+    m = W.transport_materials(geo)
+    xi = W.transport_xi(n, kmax, seed=1)
+    t0 = time.perf_counter()
+    out = O.transport(tr["x"], tr["y"], tr["z"], tr["dx"], tr["dy"], tr["dz"], node0, m["node_material"],
+                      m["sigma_n"], xi, kmax, threads=threads)
+    dt = time.perf_counter() - t0
+    res["transport"] = {"tracks_per_s": n / dt, "steps_per_s": float(out["steps"].sum()) / dt, "sample": n}
+    res["boolean"] = {}
+    for spec in W.boolean_table(3, seed=13):
+        tb = W.tracks_for_solid(spec, 100000, seed=21)
+        t0 = time.perf_counter()
+        oracle.Solid.from_spec(spec).query(**tb, threads=threads)
+        res["boolean"][spec["params"][0]] = {"queries_per_s": 100000 * N_QUERIES / (time.perf_counter() - t0)}
+    for label, g, k, mk in (("nav_nested", geo, 100000, lambda: W.nested_tracks(100000, seed=1, geom=geo)),
+                            ("nav_crowded", W.crowded_geometry(), 20000, None)):
+        Og = oracle.Geometry(g["solids"], g["nodes"])
+        tn = mk() if mk else W.crowded_tracks(g, k, seed=2, surf_frac=0.0)
+        nd = Og.locate(tn["x"], tn["y"], tn["z"], threads=threads)
+        t0 = time.perf_counter()
+        Og.nav_step(tn["x"], tn["y"], tn["z"], tn["dx"], tn["dy"], tn["dz"], nd, threads=threads)
+        res[label] = {"steps_per_s": k / (time.perf_counter() - t0), "sample": k}
+    return res
+
+
 def cpu_baseline_sweep(max_exp: int = 16):
     """The oracle on the sweep's tracks for N <= 2^max_exp, one core and all cores
     (DistanceToOut only), for the GPU-over-CPU ratio of the paper's figure."""
@@ -335,6 +373,7 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(inputs, args.cpu_sample)
         if not args.no_extra:
             line["sweep_dist_out_oracle"] = cpu_baseline_sweep()
+            line["oracle_extras"] = cpu_baseline_extras()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
