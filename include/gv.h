@@ -178,9 +178,11 @@ gv_status gv_pipeline_join(gv_pipeline* p, void* stream);
  * The scheduler of the paper (Project goals, item 1) collects particles that sit
  * in the same kind of volume into baskets and hands them to the geometry.  A
  * batch holds many such baskets, each against its own solid, over one shared
- * structure-of-arrays track set, and evaluates all of them with one persistent
- * kernel replayed from a CUDA graph (plus the binary64 worklist pass for
- * GV_FP32_REFINE). */
+ * structure-of-arrays track set, and evaluates all of them with persistent
+ * kernels replayed from a CUDA graph: GV_FP64 one kernel over all tiles;
+ * GV_FP32_REFINE one kernel per solid family present (box; trd/trap; tube;
+ * one-section cone; multi-section polycone, with lane refill; boolean, in
+ * binary64) on parallel graph branches, then the binary64 worklist pass. */
 typedef struct {
   int64_t offset;   /* first track of the basket in the shared arrays */
   int64_t n;        /* tracks in the basket (>= 0)                    */
@@ -190,7 +192,9 @@ typedef struct {
 
 /* Launch shape: threads per CTA (128, 256 or 512), tracks per thread in a tile
  * (1..16; a tile is threads * items tracks of one basket), resident CTAs per SM
- * (1..32, 0 = as many as fit). */
+ * (1..32, 0 = as many as fit).  GV_FP32_REFINE: each family kernel has its own
+ * block size (set by its registers); threads * items is the tile length and
+ * ctas_per_sm caps the resident CTAs of every family kernel. */
 typedef struct {
   int32_t threads, items, ctas_per_sm, reserved;
 } gv_batch_config;

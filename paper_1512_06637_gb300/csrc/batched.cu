@@ -1,15 +1,20 @@
-// batched.cu -- mixed-solid, mixed-size baskets in one persistent launch.
+// batched.cu -- mixed-solid, mixed-size baskets in persistent launches.
 //
 // The scheduler of the paper (Project goals, item 1) hands the geometry baskets
 // of particles that sit in the same kind of volume; here many such baskets,
-// each against its own solid, are evaluated by one persistent kernel: CTAs take
-// fixed-size tiles (never crossing a basket) from an atomic counter, stage the
-// tile's solid descriptor in shared memory when it changes, and run the binary32
-// bulk pass (or the binary64 pass) on the tile.  Uncertain tracks of every solid
-// go to one worklist of (solid, track) pairs that a second kernel recomputes in
-// binary64.  The counter reset, both kernels and the worklist pass are captured
-// once into a CUDA graph and replayed; an autotuner picks the block size, the
-// tile length and the number of resident CTAs per SM by timing graph replays.
+// each against its own solid, are cut into fixed-size tiles (never crossing a
+// basket), grouped by solid family.  Binary32: one persistent kernel per family
+// that has tiles (box; trd/trap; tube; one-section cone; multi-section polycone;
+// boolean), each with the block shape its registers allow, all captured on
+// parallel branches of one CUDA graph so that their tails overlap.  CTAs take
+// tiles from the family's atomic counter and stage the tile's solid descriptor in
+// shared memory when it changes; the polycone kernel hands tiles to warps, which
+// keep one track per lane and refill idle lanes from their tile (its walk visits
+// one to several sections); booleans, which have no binary32 form, are evaluated
+// in binary64 directly.  Uncertain tracks of every solid go to one worklist of
+// (solid, track) pairs that a last kernel recomputes in binary64.  Binary64: one
+// persistent kernel over all tiles.  An autotuner picks the tile length and the
+// resident CTAs per SM (and, in binary64, the block size) by timing graph replays.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -35,23 +40,19 @@ __device__ __forceinline__ void stage_any(Desc& dst, const Desc* __restrict__ sr
   for (int i = threadIdx.x; i < (int)(sizeof(Desc) / 16); i += blockDim.x) d[i] = s[i];
 }
 
-template <int THREADS, bool FP64>
+// Binary64: one persistent kernel over all tiles; a CTA takes a tile, stages its solid when
+// it changes and evaluates the tile's tracks one per thread.
+template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_batched(const Desc* __restrict__ solids, const Tile* __restrict__ tiles,
-                                                     int ntiles, unsigned* __restrict__ next_tile, QueryArgs a,
-                                                     unsigned long long* __restrict__ worklist,
-                                                     unsigned long long* __restrict__ wl_count) {
+                                                     int ntiles, unsigned* __restrict__ next, QueryArgs a) {
   __shared__ Desc S;
   __shared__ int s_tile;
   int loaded = -1;
   const unsigned want = (a.inside ? 1u : 0u) | (a.din ? 2u : 0u) | (a.dout ? 4u : 0u) | (a.sin ? 8u : 0u) |
                         (a.sout ? 16u : 0u);
   const bool dirs = want & 6u;
-  const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
-              *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
-              *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
-  const unsigned lane = threadIdx.x & 31u;
   for (;;) {
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(next_tile, 1u);
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(next, 1u);
     __syncthreads();
     const int t = s_tile;
     if (t >= ntiles) break;
@@ -62,60 +63,20 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_batched(const Desc* 
       __syncthreads();
     }
     const int type = S.type;
-    for (int j0 = 0; j0 < tl.len; j0 += THREADS) {
-      const int j = j0 + threadIdx.x;
-      const bool valid = j < tl.len;
+    for (int j = threadIdx.x; j < tl.len; j += THREADS) {
       const int64_t i = tl.start + j;
-      bool flag = false;
-      if (valid) {
-        if (FP64) {
-          f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
-          if (dirs) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
-          f64::Result R;
-          if (type == kBox) f64::box_query(S, T, want, R);
-          else if (type == kTrd || type == kTrap) f64::planar_query(S, T, want, R);
-          else if (type == kBool) f64::bool_query(S, T, want, R);
-          else f64::pcon_query(S, T, want, R);
-          if (a.inside) a.inside[i] = (int8_t)R.code;
-          if (a.din) a.din[i] = R.din;
-          if (a.dout) a.dout[i] = R.dout;
-          if (a.sin) a.sin[i] = R.sin;
-          if (a.sout) a.sout[i] = R.sout;
-        } else {
-          const f32::TrackF T = f32::load_track(X, Y, Z, Ux, Uy, Uz, i, dirs);
-          f32::R32 R;
-          R.flag = T.bad;
-          R.code = 1;
-          R.din = R.dout = R.sin = R.sout = 0.f;
-          if (!R.flag) {
-            if (type == kBox) f32::box32(S, T, want, R);
-            else if (type == kTrd || type == kTrap) f32::planar32(S, T, want, R);
-            else if (type == kTube) f32::pcon32<true>(S, T, want, R);
-            else if (type == kBool) R.flag = true;  // booleans: binary64 only
-            else f32::pcon32<false>(S, T, want, R);
-          }
-          flag = R.flag;
-          if (!flag) {
-            if (a.inside) a.inside[i] = (int8_t)R.code;
-            if (a.din) reinterpret_cast<unsigned long long*>(a.din)[i] = f32::f2d_bits(R.din);
-            if (a.dout) reinterpret_cast<unsigned long long*>(a.dout)[i] = f32::f2d_bits(R.dout);
-            if (a.sin) reinterpret_cast<unsigned long long*>(a.sin)[i] = f32::f2d_bits(R.sin);
-            if (a.sout) reinterpret_cast<unsigned long long*>(a.sout)[i] = f32::f2d_bits(R.sout);
-          }
-        }
-      }
-      if (!FP64) {
-        const unsigned m = __ballot_sync(0xffffffffu, flag);
-        if (m) {
-          unsigned long long at = 0;
-          const int leader = __ffs(m) - 1;
-          if ((int)lane == leader) at = atomicAdd(wl_count, (unsigned long long)__popc(m));
-          at = __shfl_sync(0xffffffffu, at, leader);
-          if (flag)
-            worklist[at + __popc(m & ((1u << lane) - 1u))] =
-                ((unsigned long long)(unsigned)tl.solid << 40) | (unsigned long long)i;
-        }
-      }
+      f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
+      if (dirs) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
+      f64::Result R;
+      if (type == kBox) f64::box_query(S, T, want, R);
+      else if (type == kTrd || type == kTrap) f64::planar_query(S, T, want, R);
+      else if (type == kBool) f64::bool_query(S, T, want, R);
+      else f64::pcon_query(S, T, want, R);
+      if (a.inside) a.inside[i] = (int8_t)R.code;
+      if (a.din) a.din[i] = R.din;
+      if (a.dout) a.dout[i] = R.dout;
+      if (a.sin) a.sin[i] = R.sin;
+      if (a.sout) a.sout[i] = R.sout;
     }
     __syncthreads();
   }
@@ -147,42 +108,292 @@ __global__ void __launch_bounds__(256) k_batched_refine(const Desc* __restrict__
   }
 }
 
-template <int THREADS, bool FP64>
-static cudaError_t launch_batched_t(int grid, const Desc* solids, const Tile* tiles, int ntiles, unsigned* next,
-                                    const QueryArgs& a, unsigned long long* wl, unsigned long long* cnt,
-                                    cudaStream_t st) {
-  k_batched<THREADS, FP64><<<grid, THREADS, 0, st>>>(solids, tiles, ntiles, next, a, wl, cnt);
-  return cudaGetLastError();
-}
+// ------------------------------------------------ binary32, one kernel per family
 
-template <int THREADS, bool FP64>
-static int occupancy_t() {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<THREADS, FP64>, THREADS, 0) != cudaSuccess) return 1;
-  return n > 0 ? n : 1;
-}
+enum : int { kFamBox = 0, kFamPlanar = 1, kFamTube = 2, kFamCone = 3, kFamWalk = 4, kFamBool = 5, kFams = 6 };
 
-static int occupancy(int threads, bool fp64) {
-  switch (threads) {
-    case 128: return fp64 ? occupancy_t<128, true>() : occupancy_t<128, false>();
-    case 512: return fp64 ? occupancy_t<512, true>() : occupancy_t<512, false>();
-    default: return fp64 ? occupancy_t<256, true>() : occupancy_t<256, false>();
+// Block shapes per family, from the registers each needs: threads and resident blocks per
+// SM (one-track-per-thread families use 256 threads, so that tiles of 128 * 2^k tracks
+// fill them).
+template <int FAM> struct BShape { static constexpr int threads = 256, blocks = 3; };
+template <> struct BShape<kFamBox> { static constexpr int threads = 256, blocks = 4; };
+template <> struct BShape<kFamWalk> { static constexpr int threads = 320, blocks = 2; };
+template <> struct BShape<kFamBool> { static constexpr int threads = 256, blocks = 2; };
+// Tiles of the polycone family hold one track per lane of a warp.
+constexpr int kWalkTile = 32;
+
+int family_of(const Desc& h) {
+  switch (h.type) {
+    case kBox: return kFamBox;
+    case kTrd:
+    case kTrap: return kFamPlanar;
+    case kTube: return kFamTube;
+    case kBool: return kFamBool;
+    default: return h.nz > 2 ? kFamWalk : kFamCone;
   }
 }
 
-static cudaError_t launch_batched(int threads, bool fp64, int grid, const Desc* solids, const Tile* tiles, int ntiles,
-                                  unsigned* next, const QueryArgs& a, unsigned long long* wl,
-                                  unsigned long long* cnt, cudaStream_t st) {
+__device__ __forceinline__ void write32(const QueryArgs& a, int64_t i, const f32::R32& R) {
+  if (a.inside) a.inside[i] = (int8_t)R.code;
+  if (a.din) reinterpret_cast<unsigned long long*>(a.din)[i] = f32::f2d_bits(R.din);
+  if (a.dout) reinterpret_cast<unsigned long long*>(a.dout)[i] = f32::f2d_bits(R.dout);
+  if (a.sin) reinterpret_cast<unsigned long long*>(a.sin)[i] = f32::f2d_bits(R.sin);
+  if (a.sout) reinterpret_cast<unsigned long long*>(a.sout)[i] = f32::f2d_bits(R.sout);
+}
+
+// A finished track: its results, or its (solid, track) pair on the refinement worklist.
+__device__ __forceinline__ void finish32(const QueryArgs& a, unsigned long long* worklist, unsigned long long* wl_count,
+                                         int solid, int64_t i, const f32::R32& R) {
+  if (R.flag) worklist[atomicAdd(wl_count, 1ull)] = ((unsigned long long)(unsigned)solid << 40) | (unsigned long long)i;
+  else write32(a, i, R);
+}
+
+__device__ __forceinline__ unsigned want_of(const QueryArgs& a) {
+  return (a.inside ? 1u : 0u) | (a.din ? 2u : 0u) | (a.dout ? 4u : 0u) | (a.sin ? 8u : 0u) | (a.sout ? 16u : 0u);
+}
+
+// One track per thread (box, trd/trap, tube, one-section cone): a CTA takes a tile, stages
+// its solid when it changes, runs the family's binary32 pass over the tile.
+template <int FAM>
+__global__ void __launch_bounds__(BShape<FAM>::threads, BShape<FAM>::blocks)
+    k_bfam32(const Desc* __restrict__ solids, const Tile* __restrict__ tiles, int ntiles, unsigned* __restrict__ next,
+             QueryArgs a, unsigned long long* __restrict__ worklist, unsigned long long* __restrict__ wl_count) {
+  constexpr int THREADS = BShape<FAM>::threads;
+  __shared__ Desc S;
+  __shared__ int s_tile;
+  int loaded = -1;
+  const unsigned want = want_of(a);
+  const bool dirs = want & 6u;
+  const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
+              *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
+              *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
+  const unsigned lane = threadIdx.x & 31u;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const Tile tl = tiles[t];
+    if (tl.solid != loaded) {
+      stage_any(S, solids + tl.solid);
+      loaded = tl.solid;
+      __syncthreads();
+    }
+    for (int j0 = 0; j0 < tl.len; j0 += THREADS) {
+      const int j = j0 + threadIdx.x;
+      const int64_t i = tl.start + j;
+      bool flag = false;
+      if (j < tl.len) {
+        const f32::TrackF T = f32::load_track(X, Y, Z, Ux, Uy, Uz, i, dirs);
+        f32::R32 R;
+        R.flag = T.bad;
+        R.code = 1;
+        R.din = R.dout = R.sin = R.sout = 0.f;
+        if (!R.flag) {
+          if (FAM == kFamBox) f32::box32(S, T, want, R);
+          else if (FAM == kFamPlanar) f32::planar32(S, T, want, R);
+          else if (FAM == kFamTube) f32::pcon32<true>(S, T, want, R);
+          else f32::pcon32<false>(S, T, want, R);
+        }
+        flag = R.flag;
+        if (!flag) write32(a, i, R);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, flag);
+      if (m) {
+        unsigned long long at = 0;
+        const int leader = __ffs(m) - 1;
+        if ((int)lane == leader) at = atomicAdd(wl_count, (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (flag)
+          worklist[at + __popc(m & ((1u << lane) - 1u))] = ((unsigned long long)(unsigned)tl.solid << 40) | (unsigned long long)i;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Multi-section polycones with lane refill: each warp keeps one track per lane; when at
+// least half its lanes are idle they take the next tracks from the family's tiles (32
+// tracks each, fetched from the family counter as the warp uses them up), so lanes of one
+// warp may hold tracks of different solids: each lane reads its solid's descriptor from
+// the table in global memory (a few KB per solid, cached).  Every busy lane then advances
+// its walk by one section.
+__global__ void __launch_bounds__(BShape<kFamWalk>::threads, BShape<kFamWalk>::blocks)
+    k_bwalk32(const Desc* __restrict__ solids, const Tile* __restrict__ tiles, int ntiles, unsigned* __restrict__ next,
+              QueryArgs a, unsigned long long* __restrict__ worklist, unsigned long long* __restrict__ wl_count) {
+  const unsigned want = want_of(a);
+  const bool dirs = want & 6u;
+  const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
+              *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
+              *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
+  const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
+  Tile tl{0, 0, 0};  // the warp's current tile (warp-uniform)
+  int pos = 0;       // its next track
+  bool more = true, busy = false;
+  int64_t i = 0;
+  int sid = 0;
+  f32::TrackF T;
+  f32::R32 R;
+  f32::Walk W;
+  while (true) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !busy);
+    if (more && (__popc(idle) >= 16 || idle == 0xffffffffu)) {
+      // hand the idle lanes, in lane order, the next tracks of the current tile and of as
+      // many further tiles as they need
+      const int need = __popc(idle), rank = __popc(idle & below);
+      int given = 0;
+      int64_t my_i = -1;
+      int my_sid = 0;
+      while (given < need) {  // warp-uniform
+        if (pos >= tl.len) {
+          int t = 0;
+          if (lane == 0) t = (int)atomicAdd(next, 1u);
+          t = __shfl_sync(0xffffffffu, t, 0);
+          if (t >= ntiles) { more = false; break; }
+          tl = tiles[t];
+          pos = 0;
+        }
+        const int take = min(tl.len - pos, need - given);
+        if (!busy && rank >= given && rank < given + take) {
+          my_i = tl.start + pos + (rank - given);
+          my_sid = tl.solid;
+        }
+        pos += take;
+        given += take;
+      }
+      if (my_i >= 0) {
+        i = my_i;
+        sid = my_sid;
+        const Desc& S = solids[sid];
+        T = f32::load_track<true>(X, Y, Z, Ux, Uy, Uz, i, dirs);
+        R.flag = T.bad;
+        R.code = 1;
+        R.din = R.dout = R.sin = R.sout = 0.f;
+        W.need_in = W.need_out = false;
+        W.live = false;
+        if (!R.flag) busy = f32::pcon_begin<false>(S, T, want, R, W);
+        if (!busy) finish32(a, worklist, wl_count, sid, i, R);
+      }
+    }
+    if (__ballot_sync(0xffffffffu, busy) == 0u) {
+      if (!more) break;
+      continue;
+    }
+    if (busy) {
+      f32::pcon_step<false>(solids[sid], T, W);
+      if (!W.live) {
+        f32::pcon_end(W, R);
+        finish32(a, worklist, wl_count, sid, i, R);
+        busy = false;
+      }
+    }
+  }
+}
+
+// Booleans: binary64 directly (no binary32 form), one track per thread.
+__global__ void __launch_bounds__(BShape<kFamBool>::threads, BShape<kFamBool>::blocks)
+    k_bbool64(const Desc* __restrict__ solids, const Tile* __restrict__ tiles, int ntiles, unsigned* __restrict__ next,
+              QueryArgs a) {
+  constexpr int THREADS = BShape<kFamBool>::threads;
+  __shared__ int s_tile;
+  const unsigned want = want_of(a);
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const Tile tl = tiles[t];
+    const Desc& S = solids[tl.solid];
+    for (int j = threadIdx.x; j < tl.len; j += THREADS) {
+      const int64_t i = tl.start + j;
+      f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
+      if (want & 6u) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
+      f64::Result R;
+      f64::bool_query(S, T, want, R);
+      if (a.inside) a.inside[i] = (int8_t)R.code;
+      if (a.din) a.din[i] = R.din;
+      if (a.dout) a.dout[i] = R.dout;
+      if (a.sin) a.sin[i] = R.sin;
+      if (a.sout) a.sout[i] = R.sout;
+    }
+    __syncthreads();
+  }
+}
+
+template <int FAM>
+static int fam_occupancy() {
+  int n = 0;
+  if constexpr (FAM == kFamWalk) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bwalk32, BShape<kFamWalk>::threads, 0) != cudaSuccess) return 1;
+  } else if constexpr (FAM == kFamBool) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bbool64, BShape<kFamBool>::threads, 0) != cudaSuccess) return 1;
+  } else {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bfam32<FAM>, BShape<FAM>::threads, 0) != cudaSuccess) return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+static int fam_occupancy(int f) {
+  switch (f) {
+    case kFamBox: return fam_occupancy<kFamBox>();
+    case kFamPlanar: return fam_occupancy<kFamPlanar>();
+    case kFamTube: return fam_occupancy<kFamTube>();
+    case kFamCone: return fam_occupancy<kFamCone>();
+    case kFamWalk: return fam_occupancy<kFamWalk>();
+    default: return fam_occupancy<kFamBool>();
+  }
+}
+
+// Launch family f over its tiles with at most per_sm resident CTAs per SM.
+static cudaError_t launch_family(int f, int per_sm, const Desc* solids, const Tile* tiles, int ntiles, unsigned* next,
+                                 const QueryArgs& a, unsigned long long* wl, unsigned long long* cnt, cudaStream_t st) {
+  const int occ = fam_occupancy(f);
+  const int cap = (per_sm > 0 ? std::min(per_sm, occ) : occ) * sm_count();
+  const int per_block = f == kFamWalk ? BShape<kFamWalk>::threads / 32 : 1;  // tiles a CTA works on at once
+  const int grid = std::max(1, std::min(cap, (ntiles + per_block - 1) / per_block));
+  // (the polycone family's tiles are one warp-refill long: a warp goes through several)
+  switch (f) {
+    case kFamBox: k_bfam32<kFamBox><<<grid, BShape<kFamBox>::threads, 0, st>>>(solids, tiles, ntiles, next, a, wl, cnt); break;
+    case kFamPlanar: k_bfam32<kFamPlanar><<<grid, BShape<kFamPlanar>::threads, 0, st>>>(solids, tiles, ntiles, next, a, wl, cnt); break;
+    case kFamTube: k_bfam32<kFamTube><<<grid, BShape<kFamTube>::threads, 0, st>>>(solids, tiles, ntiles, next, a, wl, cnt); break;
+    case kFamCone: k_bfam32<kFamCone><<<grid, BShape<kFamCone>::threads, 0, st>>>(solids, tiles, ntiles, next, a, wl, cnt); break;
+    case kFamWalk:
+      k_bwalk32<<<grid, BShape<kFamWalk>::threads, 0, st>>>(solids, tiles, ntiles, next, a, wl, cnt);
+      break;
+    default: k_bbool64<<<grid, BShape<kFamBool>::threads, 0, st>>>(solids, tiles, ntiles, next, a); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int THREADS>
+static cudaError_t launch_batched_t(int grid, const Desc* solids, const Tile* tiles, int ntiles, unsigned* next,
+                                    const QueryArgs& a, cudaStream_t st) {
+  k_batched<THREADS><<<grid, THREADS, 0, st>>>(solids, tiles, ntiles, next, a);
+  return cudaGetLastError();
+}
+
+template <int THREADS>
+static int occupancy_t() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<THREADS>, THREADS, 0) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+// resident CTAs per SM of the binary64 kernel
+static int occupancy(int threads) {
   switch (threads) {
-    case 128:
-      return fp64 ? launch_batched_t<128, true>(grid, solids, tiles, ntiles, next, a, wl, cnt, st)
-                  : launch_batched_t<128, false>(grid, solids, tiles, ntiles, next, a, wl, cnt, st);
-    case 512:
-      return fp64 ? launch_batched_t<512, true>(grid, solids, tiles, ntiles, next, a, wl, cnt, st)
-                  : launch_batched_t<512, false>(grid, solids, tiles, ntiles, next, a, wl, cnt, st);
-    default:
-      return fp64 ? launch_batched_t<256, true>(grid, solids, tiles, ntiles, next, a, wl, cnt, st)
-                  : launch_batched_t<256, false>(grid, solids, tiles, ntiles, next, a, wl, cnt, st);
+    case 128: return occupancy_t<128>();
+    case 512: return occupancy_t<512>();
+    default: return occupancy_t<256>();
+  }
+}
+
+static cudaError_t launch_batched(int threads, int grid, const Desc* solids, const Tile* tiles, int ntiles,
+                                  unsigned* next, const QueryArgs& a, cudaStream_t st) {
+  switch (threads) {
+    case 128: return launch_batched_t<128>(grid, solids, tiles, ntiles, next, a, st);
+    case 512: return launch_batched_t<512>(grid, solids, tiles, ntiles, next, a, st);
+    default: return launch_batched_t<256>(grid, solids, tiles, ntiles, next, a, st);
   }
 }
 
@@ -196,12 +407,18 @@ struct gv_batch {
   int64_t total;                          // one past the largest track index used
   std::vector<gv_basket> baskets;
   std::vector<int> solid_types;
+  std::vector<int> solid_fam;             // binary32 family of every solid
   Desc* d_solids = nullptr;
-  Tile* d_tiles = nullptr;
+  Tile* d_tiles = nullptr;                // binary32 tiles grouped by family, then the binary64 tiles
   int64_t tile_cap = 0;                   // tiles allocated
   int ntiles = 0;
-  unsigned* d_next = nullptr;             // [0] tile counter; then (8-aligned) worklist length
-  unsigned long long* d_wl = nullptr;     // worklist of (solid << 40 | track)
+  int first64 = 0, ntiles64 = 0;
+  int fam_first[kFams] = {0}, fam_count[kFams] = {0};
+  unsigned* d_next = nullptr;             // tile counters: [0] all tiles, [1 + f] family f; worklist length at byte 64
+  cudaStream_t fam_stream[kFams] = {nullptr};  // branches of the captured graph
+  cudaEvent_t fork_ev = nullptr, join_ev[kFams] = {nullptr};
+  unsigned long long* d_wl = nullptr;     // worklist of (solid << 40 | track), one segment per family
+  int64_t wl_seg[kFams] = {0};            // first entry of every family's segment
   gv_batch_config cfg{256, 2, 0, 0};
   // captured graph and the arguments it was captured with
   cudaStream_t cap_stream = nullptr;
@@ -211,14 +428,33 @@ struct gv_batch {
   gv_batch_config cap_cfg{0, 0, 0, 0};
 };
 
-static unsigned long long* wl_count_ptr(gv_batch* b) {
-  return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_next) + 8);
+// worklist length of family f (all of the binary64 kernel's tiles use none)
+static unsigned long long* wl_count_ptr(gv_batch* b, int f) {
+  return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->d_next) + 64) + f;
 }
+constexpr size_t kCounterBytes = 128;
 
 static gv_status build_tiles(gv_batch* b) {
   const int64_t tile = (int64_t)b->cfg.threads * b->cfg.items;
   std::vector<Tile> t;
   t.reserve((size_t)b->tile_cap);
+  for (int f = 0; f < kFams; f++) {  // grouped by family, baskets in order within one
+    b->fam_first[f] = (int)t.size();
+    for (const gv_basket& k : b->baskets) {
+      if (b->solid_fam[k.solid] != f) continue;
+      const int64_t len = f == kFamWalk ? kWalkTile : tile;
+      for (int64_t off = 0; off < k.n; off += len) {
+        Tile x;
+        x.start = k.offset + off;
+        x.len = (int)std::min<int64_t>(len, k.n - off);
+        x.solid = k.solid;
+        t.push_back(x);
+      }
+    }
+    b->fam_count[f] = (int)t.size() - b->fam_first[f];
+  }
+  // then the binary64 kernel's tiles: every basket in order, tiles of the configured length
+  b->first64 = (int)t.size();
   for (const gv_basket& k : b->baskets)
     for (int64_t off = 0; off < k.n; off += tile) {
       Tile x;
@@ -227,6 +463,7 @@ static gv_status build_tiles(gv_batch* b) {
       x.solid = k.solid;
       t.push_back(x);
     }
+  b->ntiles64 = (int)t.size() - b->first64;
   if ((int64_t)t.size() > b->tile_cap) return set_error(GV_ERR_INVALID_ARG, "batch: too many tiles");
   b->ntiles = (int)t.size();
   if (!t.empty()) {
@@ -254,19 +491,35 @@ static gv_status check_config(const gv_batch_config* c) {
 static gv_status capture(gv_batch* b, const QueryArgs& a, int prec) {
   drop_graph(b);
   const bool fp64 = prec == GV_FP64;
-  const int occ = occupancy(b->cfg.threads, fp64);
-  const int per_sm = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, occ) : occ;
-  const int grid = std::max(1, per_sm * sm_count());
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_error(e, "batch: begin capture");
-  cudaError_t le = cudaMemsetAsync(b->d_next, 0, 16, b->cap_stream);
-  if (le == cudaSuccess)
-    le = launch_batched(b->cfg.threads, fp64, grid, b->d_solids, b->d_tiles, b->ntiles, b->d_next, a, b->d_wl,
-                        wl_count_ptr(b), b->cap_stream);
+  cudaError_t le = cudaMemsetAsync(b->d_next, 0, kCounterBytes, b->cap_stream);
+  if (le == cudaSuccess && fp64) {
+    const int occ = occupancy(b->cfg.threads);
+    const int per_sm = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, occ) : occ;
+    le = launch_batched(b->cfg.threads, std::max(1, per_sm * sm_count()), b->d_solids, b->d_tiles + b->first64, b->ntiles64,
+                        b->d_next, a, b->cap_stream);
+  }
   if (le == cudaSuccess && !fp64) {
-    k_batched_refine<<<sm_count() * 2, 256, 0, b->cap_stream>>>(b->d_solids, a, b->d_wl, wl_count_ptr(b));
-    le = cudaGetLastError();
+    // the families on parallel branches, each followed by the binary64 pass over its own
+    // worklist segment (a refinement's latency then overlaps the other families' work)
+    le = cudaEventRecord(b->fork_ev, b->cap_stream);
+    for (int f = 0; f < kFams && le == cudaSuccess; f++) {
+      if (b->fam_count[f] == 0) continue;
+      cudaStream_t fs = b->fam_stream[f];
+      unsigned long long* wl = b->d_wl + b->wl_seg[f];
+      le = cudaStreamWaitEvent(fs, b->fork_ev, 0);
+      if (le == cudaSuccess)
+        le = launch_family(f, b->cfg.ctas_per_sm, b->d_solids, b->d_tiles + b->fam_first[f], b->fam_count[f],
+                           b->d_next + 1 + f, a, wl, wl_count_ptr(b, f), fs);
+      if (le == cudaSuccess && f != kFamBool) {
+        k_batched_refine<<<sm_count() * 2, 256, 0, fs>>>(b->d_solids, a, wl, wl_count_ptr(b, f));
+        le = cudaGetLastError();
+      }
+      if (le == cudaSuccess) le = cudaEventRecord(b->join_ev[f], fs);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap_stream, b->join_ev[f], 0);
+    }
   }
   e = cudaStreamEndCapture(b->cap_stream, &g);
   if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_error(le, "batch: capture launch"); }
@@ -313,7 +566,7 @@ gv_status gv_batch_create(const gv_solid* const* solids, int32_t nsolids, const 
       return set_error(GV_ERR_INVALID_ARG, "batch: basket with a negative offset/size or an unknown solid");
     if (k.offset + k.n > ((int64_t)1 << 40)) return set_error(GV_ERR_UNSUPPORTED, "batch: track index beyond 2^40");
     total = std::max(total, k.offset + k.n);
-    tile_cap += (k.n + 127) / 128;
+    tile_cap += (k.n + 31) / 32 + (k.n + 127) / 128;  // binary32 tiles (at least 32 tracks), binary64 (128)
   }
   for (int i = 0; i < nsolids; i++)
     if (!solids[i]) return set_error(GV_ERR_INVALID_ARG, "batch: NULL solid");
@@ -326,7 +579,10 @@ gv_status gv_batch_create(const gv_solid* const* solids, int32_t nsolids, const 
   b->baskets.assign(baskets, baskets + nbaskets);
   b->tile_cap = std::max<int64_t>(tile_cap, 1);
   cudaError_t e = cudaGetDevice(&b->device);
-  for (int i = 0; i < nsolids; i++) b->solid_types.push_back(solids[i]->h.type);
+  for (int i = 0; i < nsolids; i++) {
+    b->solid_types.push_back(solids[i]->h.type);
+    b->solid_fam.push_back(family_of(solids[i]->h));
+  }
   const int nrec = table_size(solids, nsolids);  // booleans carry their components along
   if (e == cudaSuccess) e = cudaMalloc(&b->d_solids, sizeof(Desc) * nrec);
   if (e == cudaSuccess) {
@@ -334,10 +590,21 @@ gv_status gv_batch_create(const gv_solid* const* solids, int32_t nsolids, const 
     e = cudaMemcpy(b->d_solids, h.data(), sizeof(Desc) * nrec, cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(Tile) * b->tile_cap);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_next, 64);
-  if (e == cudaSuccess) e = cudaMemset(b->d_next, 0, 64);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_wl, sizeof(unsigned long long) * (size_t)std::max<int64_t>(total, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_next, kCounterBytes);
+  if (e == cudaSuccess) e = cudaMemset(b->d_next, 0, kCounterBytes);
+  int64_t wl_total = 0;  // a family's segment holds every track of its baskets
+  for (int f = 0; f < kFams; f++) {
+    b->wl_seg[f] = wl_total;
+    for (const gv_basket& k : b->baskets)
+      if (b->solid_fam[k.solid] == f) wl_total += k.n;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_wl, sizeof(unsigned long long) * (size_t)std::max<int64_t>(wl_total, 1));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  for (int f = 0; f < kFams && e == cudaSuccess; f++) {
+    e = cudaStreamCreateWithFlags(&b->fam_stream[f], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[f], cudaEventDisableTiming);
+  }
   gv_status st = GV_OK;
   if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? set_error(GV_ERR_OUT_OF_MEMORY, "batch: cudaMalloc failed")
                                                            : cuda_error(e, "batch: create");
@@ -381,12 +648,14 @@ gv_status gv_batch_run(gv_batch* b, const gv_tracks* t, gv_precision prec, const
 
 gv_status gv_batch_refined(gv_batch* b, void* stream, int64_t* n) {
   if (!b || !n) return set_error(GV_ERR_INVALID_ARG, "batch: NULL argument");
-  unsigned long long h = 0;
+  unsigned long long h[kFams] = {0};
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(&h, wl_count_ptr(b), sizeof(h), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(h, wl_count_ptr(b, 0), sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "gv_batch_refined");
-  *n = (int64_t)h;
+  int64_t sum = 0;
+  for (int f = 0; f < kFams; f++) sum += (int64_t)h[f];
+  *n = sum;
   return GV_OK;
 }
 
@@ -433,8 +702,10 @@ gv_status gv_batch_autotune(gv_batch* b, const gv_tracks* t, gv_precision prec, 
   cudaStream_t s = (cudaStream_t)stream;
   const int thr[3] = {128, 256, 512};
   const int items[3] = {1, 2, 4};
+  int occ32 = 1;  // binary32: the most CTAs per SM any family kernel can hold
+  for (int f = 0; f < kFams; f++) occ32 = std::max(occ32, fam_occupancy(f));
   for (int ti = 0; ti < 3; ti++) {
-    const int occ = occupancy(thr[ti], prec == GV_FP64);
+    const int occ = prec == GV_FP64 ? occupancy(thr[ti]) : occ32;
     for (int ii = 0; ii < 3; ii++) {
       for (int c = 1; c <= occ; c++) {
         gv_batch_config cfg{thr[ti], items[ii], c, 0};
@@ -474,6 +745,11 @@ void gv_batch_destroy(gv_batch* b) {
   if (!b) return;
   drop_graph(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (int f = 0; f < kFams; f++) {
+    if (b->fam_stream[f]) cudaStreamDestroy(b->fam_stream[f]);
+    if (b->join_ev[f]) cudaEventDestroy(b->join_ev[f]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->d_solids) cudaFree(b->d_solids);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_next) cudaFree(b->d_next);
