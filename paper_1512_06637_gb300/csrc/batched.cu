@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(256) k_batched_refine(const Desc* __restrict__
                         (a.sout ? 16u : 0u);
   const int64_t nref = (int64_t)*wl_count;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nref; j += stride) {
+  // consecutive entries go to consecutive blocks: a short worklist is spread over every
+  // SM instead of filling the first few blocks (each entry is a long binary64 chain)
+  for (int64_t j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; j < nref; j += stride) {
     const unsigned long long e = worklist[j];
     const int64_t i = (int64_t)(e & ((1ull << 40) - 1));
     const Desc& S = solids[e >> 40];

@@ -335,7 +335,9 @@ __global__ void __launch_bounds__(256) k_nav_refine(const NodeD* __restrict__ no
                                                     const unsigned long long* __restrict__ cnt, Vox vox) {
   const int64_t m = (int64_t)*cnt;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+  // consecutive entries go to consecutive blocks: a short worklist is spread over every
+  // SM instead of filling the first few blocks (each entry is a long binary64 chain)
+  for (int64_t j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; j < m; j += stride)
     nav_step64(nodes, children, solids, nnodes, a, wl[j], vox);
 }
 

@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(256) k_refine_fp64(const Desc* __restrict__ de
                         (a.sout ? f64::kWantSout : 0u);
   const int64_t nref = (int64_t)*counter;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nref; j += stride) {
+  // consecutive entries go to consecutive blocks: a short worklist is spread over every
+  // SM instead of filling the first few blocks (each entry is a long binary64 chain)
+  for (int64_t j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; j < nref; j += stride) {
     const int64_t i = worklist[j];
     f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
     if (want & (f64::kWantDin | f64::kWantDout)) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
