@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, navigation and serving forms")
+    ap.add_argument("--form", default="all", choices=["all", "batched"],
+                    help="batched: only the batched form, fixed launch shape, --warmup then --steps graph replays")
     return ap.parse_args()
 
 
@@ -739,10 +741,30 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
 
 
+def run_batched_only(args):
+    """The batched form alone (for profiling): launch shape 256 threads x 2 tracks, as many
+    CTAs as fit, W warm-up and K timed graph replays, FP32 + refinement."""
+    import torch
+    import paper_1512_06637_gb300 as gv
+    work = W.batched()
+    n = len(work["tracks"]["x"])
+    dev = {k: torch.from_numpy(v).cuda() for k, v in work["tracks"].items()}
+    b = gv.Batch([gv.Solid.from_spec(sp) for sp in work["solids"]], work["offset"], work["n"], work["solid"])
+    b.set_config(256, 2, 0)
+    out = gv.alloc_results(n, "cuda")
+    for _ in range(args.warmup):
+        b.run(dev, out)
+    ms = _timed(torch, lambda: b.run(dev, out), max(1, args.steps))
+    print(json.dumps({"form": "batched", "tracks": n, "ms": ms, "queries_per_s": n * N_QUERIES / (ms * 1e-3),
+                      "refined": b.refined()}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "batched":
+        run_batched_only(args)
     else:
         run_ours(args)
 
