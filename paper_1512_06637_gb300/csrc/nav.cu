@@ -397,6 +397,19 @@ __device__ __forceinline__ f32::TrackF to_local32(const NodeD& N, const f32::Tra
   return L;
 }
 
+// The planar and polycone-family passes are called, not inlined: inlined into the
+// navigation kernel, the union of every family's code needed 247 registers (one block per
+// SM); called, the kernel fits two blocks per SM (boxes, the common daughters, stay inline).
+__device__ __noinline__ void planar32_call(const Desc& S, const f32::TrackF& T, unsigned want, f32::R32& R) {
+  f32::planar32<true>(S, T, want, R);
+}
+__device__ __noinline__ void tube32_call(const Desc& S, const f32::TrackF& T, unsigned want, f32::R32& R) {
+  f32::pcon32<true, true>(S, T, want, R);
+}
+__device__ __noinline__ void pcon32_call(const Desc& S, const f32::TrackF& T, unsigned want, f32::R32& R) {
+  f32::pcon32<false, true>(S, T, want, R);
+}
+
 __device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, unsigned want, f32::R32& R) {
   R.flag = T.bad;
   R.code = 1;
@@ -404,10 +417,10 @@ __device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, uns
   if (R.flag) return;
   // frame tracks: the bounds add the local coordinates' and direction's own errors
   if (S.type == kBox) f32::box32<true>(S, T, want, R);
-  else if (S.type == kTrd || S.type == kTrap) f32::planar32<true>(S, T, want, R);
-  else if (S.type == kTube) f32::pcon32<true, true>(S, T, want, R);
+  else if (S.type == kTrd || S.type == kTrap) planar32_call(S, T, want, R);
+  else if (S.type == kTube) tube32_call(S, T, want, R);
   else if (S.type == kBool) R.flag = true;  // booleans: binary64 only
-  else f32::pcon32<false, true>(S, T, want, R);
+  else pcon32_call(S, T, want, R);
 }
 
 // half of the output tolerance: the certified binary32 results are within it
@@ -450,7 +463,7 @@ __device__ __forceinline__ void group_merge(unsigned mask, Top2<DEDUP>& top) {
 // WALK: the geometry has nodes whose daughters the pass finds by walking their grid (the
 // instance without it keeps the registers of the plain scan).
 template <bool WALK>
-__global__ void __launch_bounds__(256) k_nav_fp32(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+__global__ void __launch_bounds__(256, 2) k_nav_fp32(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                   const Desc* __restrict__ solids, int nnodes, NavArgs a,
                                                   uint32_t* __restrict__ wl, unsigned long long* __restrict__ cnt,
                                                   Vox vox) {
