@@ -723,43 +723,91 @@ __device__ __forceinline__ void flight_end(const TransportArgs& a, int64_t i, co
   a.tie[i] = F.near ? 1 : 0;
 }
 
-// Binary64, lane refill: tracks take from one to kmax steps, so each warp owns a
-// contiguous range of tracks and keeps one in each lane; when at least half its lanes are
-// idle they take the next tracks of the range, then every busy lane takes one step.
-__global__ void __launch_bounds__(256) k_transport(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                                   const Desc* __restrict__ solids, TransportArgs a, Vox vox) {
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
-  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const int64_t chunk = (a.n + nwarps - 1) / nwarps;
-  const int64_t end = (warp + 1) * chunk < a.n ? (warp + 1) * chunk : a.n;
-  int64_t next = warp * chunk;  // warp-uniform
-  const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
-  bool busy = false;
-  int64_t i = 0;
-  Flight F;
+// Binary64, in baskets (the paper's scheduler gathers particles that sit in the same kind
+// of volume, so that they run the same code): a block keeps a pool of one track per
+// thread in shared memory and loops: dead slots take the next tracks of the block's range;
+// the live tracks are ordered by the kind of volume they are in (solid type, whether the
+// volume has daughters and a grid), so that each warp steps tracks of one kind and its
+// lanes follow one path through the geometry; every thread then takes one step for the
+// track of its rank.  Tracks take from one to kmax steps; the pool keeps the block busy
+// until its range is used up.
+constexpr int kTransportThreads = 256;
+constexpr int kKinds = 32;  // volume kinds (the last one: an empty slot)
+
+__device__ __forceinline__ int volume_kind(const NodeD* __restrict__ nodes, const Desc* __restrict__ solids, int32_t v,
+                                           const Vox& vox) {
+  const NodeD& N = nodes[v];
+  const int type = solids[N.desc].type;  // 0..6
+  return type * 4 + (N.count > 0 ? 2 : 0) + (vox.grids && N.grid >= 0 ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(kTransportThreads) k_transport(const NodeD* __restrict__ nodes,
+                                                                 const int32_t* __restrict__ children,
+                                                                 const Desc* __restrict__ solids, TransportArgs a,
+                                                                 Vox vox) {
+  constexpr int B = kTransportThreads;
+  __shared__ double sp[3][B], sd[3][B], slen[B];
+  __shared__ int64_t sidx[B];
+  __shared__ int32_t sv[B], sk[B], swhy[B];
+  __shared__ unsigned char snear[B], slive[B];
+  __shared__ int sperm[B];
+  __shared__ int scount[kKinds];
+  __shared__ unsigned long long snext;
+  const int t = threadIdx.x;
+  const int64_t chunk = (a.n + gridDim.x - 1) / gridDim.x;
+  const int64_t begin = (int64_t)blockIdx.x * chunk;
+  const int64_t end = begin + chunk < a.n ? begin + chunk : a.n;
+  if (t == 0) snext = (unsigned long long)(begin < end ? begin : end);
+  slive[t] = 0;
+  __syncthreads();
   while (true) {
-    const unsigned idle = __ballot_sync(0xffffffffu, !busy);
-    if (next < end && (__popc(idle) >= 16 || idle == 0xffffffffu)) {
-      const int64_t j = next + __popc(idle & below);
-      next += __popc(idle);
-      if (!busy && j < end) {
-        i = j;
-        flight_begin(a, i, F);
-        busy = F.live;
-        if (!busy) flight_end(a, i, F);
+    // dead slots take the next tracks of the range
+    if (!slive[t]) {
+      const unsigned long long j = atomicAdd(&snext, 1ull);
+      if ((int64_t)j < end) {
+        Flight F;
+        flight_begin(a, (int64_t)j, F);
+        if (F.live) {
+          for (int c = 0; c < 3; c++) { sp[c][t] = F.p[c]; sd[c][t] = F.d[c]; }
+          slen[t] = F.len; sidx[t] = (int64_t)j; sv[t] = F.v; sk[t] = F.k; swhy[t] = F.why;
+          snear[t] = F.near; slive[t] = 1;
+        } else {
+          flight_end(a, (int64_t)j, F);
+        }
       }
     }
-    if (__ballot_sync(0xffffffffu, busy) == 0u) {
-      if (next >= end) break;
-      continue;
+    if (t < kKinds) scount[t] = 0;
+    __syncthreads();
+    const bool live = slive[t];
+    if (!__syncthreads_or(live ? 1 : ((int64_t)snext < end ? 1 : 0))) break;
+    // order the live tracks by volume kind (counting sort; empty slots last)
+    const int kind = live ? volume_kind(nodes, solids, sv[t], vox) : kKinds - 1;
+    atomicAdd(&scount[kind], 1);
+    __syncthreads();
+    if (t == 0) {
+      int acc = 0;
+      for (int k = 0; k < kKinds; k++) { const int c = scount[k]; scount[k] = acc; acc += c; }
     }
-    if (busy) {
+    __syncthreads();
+    sperm[atomicAdd(&scount[kind], 1)] = t;
+    __syncthreads();
+    // one step for the track of rank t
+    const int s = sperm[t];
+    if (slive[s]) {
+      Flight F;
+      for (int c = 0; c < 3; c++) { F.p[c] = sp[c][s]; F.d[c] = sd[c][s]; }
+      F.len = slen[s]; F.v = sv[s]; F.k = sk[s]; F.why = swhy[s]; F.near = snear[s]; F.live = true;
+      const int64_t i = sidx[s];
       flight_step(nodes, children, solids, a, i, F, vox);
-      if (!F.live) {
+      if (F.live) {
+        for (int c = 0; c < 3; c++) { sp[c][s] = F.p[c]; sd[c][s] = F.d[c]; }
+        slen[s] = F.len; sv[s] = F.v; sk[s] = F.k; swhy[s] = F.why; snear[s] = F.near;
+      } else {
         flight_end(a, i, F);
-        busy = false;
+        slive[s] = 0;
       }
     }
+    __syncthreads();
   }
 }
 
@@ -1019,9 +1067,18 @@ gv_status gv_transport(const gv_geom* g, const gv_tracks* t, const int32_t* node
   if ((uintptr_t)out->z & 7u) return set_error(GV_ERR_INVALID_ARG, "transport: arrays must be 8-byte aligned");
   TransportArgs a{t->x, t->y, t->z, t->dx, t->dy, t->dz, node0, node_material, sigma_n, xi, kmax, nmat, g->nnodes,
                   out->reason, out->steps, out->x, out->y, out->z, out->path, out->last, out->tie, t->n};
+  // Resident blocks only: each block owns a contiguous range of tracks and keeps its pool
+  // full from it, so it drains (slots empty while its last tracks finish) once per range.
+  static int resident = 0;
+  if (resident == 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport, kTransportThreads, 0) != cudaSuccess || nb < 1) nb = 1;
+    resident = nb;
+  }
   const int sms = sm_count();
-  const int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sms * 8);
-  k_transport<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, a, vox_of(g));
+  const int64_t blocks = std::min<int64_t>((t->n + kTransportThreads - 1) / kTransportThreads, (int64_t)sms * resident);
+  k_transport<<<(unsigned)blocks, kTransportThreads, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, a,
+                                                                                  vox_of(g));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GV_OK : cuda_error(e, "transport launch");
 }
