@@ -660,6 +660,7 @@ struct Flight {
   double p[3], d[3], len;
   int32_t v, k, why;
   bool near, live;
+  bool reloc;  // at a boundary, to be located again (the second half of a step)
 };
 
 __device__ __forceinline__ void flight_begin(const TransportArgs& a, int64_t i, Flight& F) {
@@ -669,13 +670,15 @@ __device__ __forceinline__ void flight_begin(const TransportArgs& a, int64_t i, 
   F.k = 0;
   F.why = GV_TRUNCATED;
   F.near = false;
+  F.reloc = false;
   F.len = 0.0;
   F.live = F.v >= 0 && F.v < a.nnodes && a.kmax > 0;
   if (F.v < 0) F.why = GV_ESCAPED;
   else if (F.v >= a.nnodes) F.why = GV_LOST;
 }
 
-// One step of the loop of the Physics subsection (see gv.h) for track i.
+// The first half of one step of the loop of the Physics subsection (see gv.h) for track i:
+// the boundary distance, the physics step and, when the process acts first, the process.
 __device__ inline void flight_step(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                    const Desc* __restrict__ solids, const TransportArgs& a, int64_t i, Flight& F,
                                    const Vox& vox) {
@@ -702,15 +705,25 @@ __device__ inline void flight_step(const NodeD* __restrict__ nodes, const int32_
     double sb, cb;
     sincos(b, &sb, &cb);
     F.d[0] = xmul(sa, cb); F.d[1] = xmul(sa, sb); F.d[2] = ca;
-  } else {  // to the boundary, then locate the probe point past it
+  } else {  // to the boundary; the probe point past it is located by flight_locate
     for (int j = 0; j < 3; j++) F.p[j] = xadd(F.p[j], xmul(dgeo, F.d[j]));
     F.len = xadd(F.len, dgeo);
-    bool surf = false;
-    F.v = locate64_surf(nodes, children, solids, xadd(F.p[0], xmul(kPush, F.d[0])),
-                        xadd(F.p[1], xmul(kPush, F.d[1])), xadd(F.p[2], xmul(kPush, F.d[2])), surf, vox);
-    F.near |= surf;
-    if (F.v < 0) { F.why = GV_ESCAPED; F.live = false; return; }
+    F.reloc = true;
+    return;
   }
+  if (F.k >= a.kmax) F.live = false;  // truncated
+}
+
+// The second half of a step that ended at a boundary: locate the probe point past it.
+__device__ inline void flight_locate(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                     const Desc* __restrict__ solids, const TransportArgs& a, Flight& F,
+                                     const Vox& vox) {
+  bool surf = false;
+  F.reloc = false;
+  F.v = locate64_surf(nodes, children, solids, xadd(F.p[0], xmul(kPush, F.d[0])), xadd(F.p[1], xmul(kPush, F.d[1])),
+                      xadd(F.p[2], xmul(kPush, F.d[2])), surf, vox);
+  F.near |= surf;
+  if (F.v < 0) { F.why = GV_ESCAPED; F.live = false; return; }
   if (F.k >= a.kmax) F.live = false;  // truncated
 }
 
@@ -749,7 +762,7 @@ __global__ void __launch_bounds__(kTransportThreads) k_transport(const NodeD* __
   __shared__ double sp[3][B], sd[3][B], slen[B];
   __shared__ int64_t sidx[B];
   __shared__ int32_t sv[B], sk[B], swhy[B];
-  __shared__ unsigned char snear[B], slive[B];
+  __shared__ unsigned char snear[B], slive[B], sreloc[B];
   __shared__ int sperm[B];
   __shared__ int scount[kKinds];
   __shared__ unsigned long long snext;
@@ -791,21 +804,50 @@ __global__ void __launch_bounds__(kTransportThreads) k_transport(const NodeD* __
     __syncthreads();
     sperm[atomicAdd(&scount[kind], 1)] = t;
     __syncthreads();
-    // one step for the track of rank t
-    const int s = sperm[t];
+    // first half of a step for the track of rank t
+    int s = sperm[t];
+    sreloc[t] = 0;
+    __syncthreads();
     if (slive[s]) {
       Flight F;
       for (int c = 0; c < 3; c++) { F.p[c] = sp[c][s]; F.d[c] = sd[c][s]; }
-      F.len = slen[s]; F.v = sv[s]; F.k = sk[s]; F.why = swhy[s]; F.near = snear[s]; F.live = true;
+      F.len = slen[s]; F.v = sv[s]; F.k = sk[s]; F.why = swhy[s]; F.near = snear[s]; F.live = true; F.reloc = false;
       const int64_t i = sidx[s];
       flight_step(nodes, children, solids, a, i, F, vox);
       if (F.live) {
         for (int c = 0; c < 3; c++) { sp[c][s] = F.p[c]; sd[c][s] = F.d[c]; }
-        slen[s] = F.len; sv[s] = F.v; sk[s] = F.k; swhy[s] = F.why; snear[s] = F.near;
+        slen[s] = F.len; sv[s] = F.v; sk[s] = F.k; swhy[s] = F.why; snear[s] = F.near; sreloc[s] = F.reloc;
       } else {
         flight_end(a, i, F);
         slive[s] = 0;
       }
+    }
+    // second half for the tracks at a boundary, gathered into the first warps
+    if (t < 2) scount[t] = 0;
+    __syncthreads();
+    const int rk = sreloc[t] ? 0 : 1;
+    if (rk == 0) atomicAdd(&scount[0], 1);
+    __syncthreads();
+    const int nreloc = scount[0];
+    __syncthreads();
+    if (t == 0) { scount[0] = 0; scount[1] = nreloc; }
+    __syncthreads();
+    sperm[atomicAdd(&scount[rk], 1)] = t;
+    __syncthreads();
+    s = sperm[t];
+    if (t < nreloc) {
+      Flight F;
+      for (int c = 0; c < 3; c++) { F.p[c] = sp[c][s]; F.d[c] = sd[c][s]; }
+      F.len = slen[s]; F.v = sv[s]; F.k = sk[s]; F.why = swhy[s]; F.near = snear[s]; F.live = true; F.reloc = true;
+      const int64_t i = sidx[s];
+      flight_locate(nodes, children, solids, a, F, vox);
+      if (F.live) {
+        sv[s] = F.v; snear[s] = F.near;
+      } else {
+        flight_end(a, i, F);
+        slive[s] = 0;
+      }
+      sreloc[s] = 0;
     }
     __syncthreads();
   }
