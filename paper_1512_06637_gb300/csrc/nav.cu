@@ -744,7 +744,7 @@ __device__ __forceinline__ void flight_end(const TransportArgs& a, int64_t i, co
 // lanes follow one path through the geometry; every thread then takes one step for the
 // track of its rank.  Tracks take from one to kmax steps; the pool keeps the block busy
 // until its range is used up.
-constexpr int kTransportThreads = 256;
+constexpr int kTransportThreads = 512;
 constexpr int kKinds = 32;  // volume kinds (the last one: an empty slot)
 
 __device__ __forceinline__ int volume_kind(const NodeD* __restrict__ nodes, const Desc* __restrict__ solids, int32_t v,
