@@ -322,11 +322,53 @@ __device__ inline void nav_step64(const NodeD* __restrict__ nodes, const int32_t
   a.next[i] = have ? who : -1;
 }
 
+// Volume kinds for gathering tracks that run the same code (the paper's baskets of
+// particles in one kind of volume): solid type, whether the volume has daughters and a grid.
+constexpr int kKinds = 32;  // volume kinds (the last one: an empty slot)
+
+__device__ __forceinline__ int volume_kind(const NodeD* __restrict__ nodes, const Desc* __restrict__ solids, int32_t v,
+                                           const Vox& vox) {
+  const NodeD& N = nodes[v];
+  const int type = solids[N.desc].type;  // 0..6
+  return type * 4 + (N.count > 0 ? 2 : 0) + (vox.grids && N.grid >= 0 ? 1 : 0);
+}
+
+// Order the m entries of a block by kind (counting sort in shared memory): perm[r] is the
+// entry of rank r.  Block-uniform: every thread of the block calls it.
+__device__ __forceinline__ void order_by_kind(int kind, int m, int* scount, int* perm) {
+  const int t = threadIdx.x;
+  if (t < kKinds) scount[t] = 0;
+  __syncthreads();
+  if (t < m) atomicAdd(&scount[kind], 1);
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int k = 0; k < kKinds; k++) { const int c = scount[k]; scount[k] = acc; acc += c; }
+  }
+  __syncthreads();
+  if (t < m) perm[atomicAdd(&scount[kind], 1)] = t;
+  __syncthreads();
+}
+
+// One thread per track; the block's 256 tracks are taken in order of the kind of volume
+// they are in, so that a warp runs one path through the geometry.
 __global__ void __launch_bounds__(256) k_nav_fp64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                   const Desc* __restrict__ solids, int nnodes, NavArgs a, Vox vox) {
+  __shared__ int scount[kKinds];
+  __shared__ int sperm[256];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
-    nav_step64(nodes, children, solids, nnodes, a, i, vox);
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {  // block-uniform
+    const int64_t i0 = base + threadIdx.x;
+    int kind = kKinds - 1;
+    if (i0 < a.n) {
+      const int32_t v = a.node[i0];
+      kind = (v >= 0 && v < nnodes) ? volume_kind(nodes, solids, v, vox) : kKinds - 2;
+    }
+    order_by_kind(kind, blockDim.x, scount, sperm);
+    const int64_t i = base + sperm[threadIdx.x];
+    if (i < a.n) nav_step64(nodes, children, solids, nnodes, a, i, vox);
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(256) k_nav_refine(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
@@ -476,8 +518,18 @@ __global__ void __launch_bounds__(256, 2) k_nav_fp32(const NodeD* __restrict__ n
   const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
               *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
               *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
-  for (int64_t base = (int64_t)blockIdx.x * tracks_per_block; base < a.n; base += stride) {
-    const int64_t i = base + threadIdx.x / kLanes;
+  __shared__ int scount[kKinds];
+  __shared__ int sperm[256];
+  for (int64_t base = (int64_t)blockIdx.x * tracks_per_block; base < a.n; base += stride) {  // block-uniform
+    // the block's tracks in order of the kind of volume they are in (a warp's four tracks
+    // then mostly run the same path)
+    int kind = kKinds - 1;
+    if (threadIdx.x < tracks_per_block && base + threadIdx.x < a.n) {
+      const int32_t v0 = a.node[base + threadIdx.x];
+      kind = (v0 >= 0 && v0 < nnodes) ? volume_kind(nodes, solids, v0, vox) : kKinds - 2;
+    }
+    order_by_kind(kind, (int)tracks_per_block, scount, sperm);
+    const int64_t i = base + sperm[threadIdx.x / kLanes];
     const bool valid = i < a.n;
     bool flag = false;
     Top2<WALK> top{F_INF, 0.f, F_INF, 0.f, kNone, kNone};
@@ -745,14 +797,6 @@ __device__ __forceinline__ void flight_end(const TransportArgs& a, int64_t i, co
 // track of its rank.  Tracks take from one to kmax steps; the pool keeps the block busy
 // until its range is used up.
 constexpr int kTransportThreads = 512;
-constexpr int kKinds = 32;  // volume kinds (the last one: an empty slot)
-
-__device__ __forceinline__ int volume_kind(const NodeD* __restrict__ nodes, const Desc* __restrict__ solids, int32_t v,
-                                           const Vox& vox) {
-  const NodeD& N = nodes[v];
-  const int type = solids[N.desc].type;  // 0..6
-  return type * 4 + (N.count > 0 ? 2 : 0) + (vox.grids && N.grid >= 0 ? 1 : 0);
-}
 
 __global__ void __launch_bounds__(kTransportThreads) k_transport(const NodeD* __restrict__ nodes,
                                                                  const int32_t* __restrict__ children,
