@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, navigation and serving forms")
-    ap.add_argument("--form", default="all", choices=["all", "batched"],
-                    help="batched: only the batched form, fixed launch shape, --warmup then --steps graph replays")
+    ap.add_argument("--form", default="all", choices=["all", "batched", "transport"],
+                    help="batched / transport: only that form (for profiling), --warmup then --steps calls")
     return ap.parse_args()
 
 
@@ -759,12 +759,34 @@ def run_batched_only(args):
                       "refined": b.refined()}), flush=True)
 
 
+def run_transport_only(args, n=1 << 17, kmax=64):
+    """The transport loop alone (for profiling): nested detector, 2^17 tracks, kmax 64."""
+    import torch
+    import paper_1512_06637_gb300 as gv
+    geo = W.nested_geometry()
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    dev = {k: torch.from_numpy(v).cuda() for k, v in W.nested_tracks(n, seed=11, geom=geo).items()}
+    node0 = G.locate(dev)
+    m = W.transport_materials(geo)
+    mat = torch.from_numpy(m["node_material"]).cuda()
+    sig = torch.from_numpy(m["sigma_n"]).cuda()
+    xi = torch.from_numpy(W.transport_xi(n, kmax, seed=1)).cuda()
+    out = G.transport(dev, node0, mat, sig, xi, kmax)
+    for _ in range(args.warmup):
+        G.transport(dev, node0, mat, sig, xi, kmax, out=out)
+    ms = _timed(torch, lambda: G.transport(dev, node0, mat, sig, xi, kmax, out=out), max(1, args.steps))
+    steps = int(out["steps"].sum().item())
+    print(json.dumps({"form": "transport", "tracks": n, "ms": ms, "steps_per_s": steps / (ms * 1e-3)}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.form == "batched":
         run_batched_only(args)
+    elif args.form == "transport":
+        run_transport_only(args)
     else:
         run_ours(args)
 
