@@ -296,7 +296,12 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* tracks, const int32_t* 
  * dgeo, the two nearest boundaries as close, or a relocation probe on a surface) - such
  * a track may legitimately differ from another evaluation of the same loop.
  * All arrays are device arrays; node_material has one entry per node (a material index
- * outside [0, nmat) ends the track as GV_LOST); async on `stream`. */
+ * outside [0, nmat) ends the track as GV_LOST); async on `stream`.
+ * prec: GV_FP64 evaluates every candidate boundary and every code of the relocation in
+ * binary64; GV_FP32_REFINE ranks them in binary32 first and evaluates in binary64 only the
+ * nearest boundary when the binary32 pass certifies it (else every candidate), and takes the
+ * relocation's codes in binary32 when all are certified (else binary64).  The results are
+ * the same bits either way. */
 enum { GV_ESCAPED = 0, GV_ABSORBED = 1, GV_TRUNCATED = 2, GV_LOST = 3 };
 typedef struct {
   int8_t* reason;
@@ -308,7 +313,8 @@ typedef struct {
 } gv_transport_out;
 gv_status gv_transport(const gv_geom* g, const gv_tracks* tracks, const int32_t* node0,
                        const int32_t* node_material, const double* sigma_n, int32_t nmat,
-                       const double* xi, int32_t kmax, const gv_transport_out* out, void* stream);
+                       const double* xi, int32_t kmax, gv_precision prec,
+                       const gv_transport_out* out, void* stream);
 
 /* --- serving: continuous batching of navigation requests (Project goals, item 1:
  *     the scheduler keeps handing baskets to the geometry) --------------------

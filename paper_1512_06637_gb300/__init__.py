@@ -305,9 +305,10 @@ class Geometry:
         return out
 
     def transport(self, tracks: dict, node0, node_material, sigma_n, xi, kmax: int, out: dict | None = None,
-                  stream=None) -> dict:
+                  stream=None, precision: str = "fp64") -> dict:
         """The transport loop (gv_transport): CUDA tensors; ``node_material`` int32 per node,
-        ``sigma_n`` float64 (nmat, 2), ``xi`` float64 (n, kmax, 4) in (0, 1]."""
+        ``sigma_n`` float64 (nmat, 2), ``xi`` float64 (n, kmax, 4) in (0, 1].  ``precision``
+        "fp32_refine" ranks candidates and codes in binary32 first (same results)."""
         import torch
         n = tracks["x"].numel()
         dev = tracks["x"].device
@@ -328,7 +329,7 @@ class Geometry:
         t = tracks_struct(tracks)
         o = _abi.TransportOut(*(_ptr(out[k]) for k in ("reason", "steps", "x", "y", "z", "path", "last", "tie")))
         check(lib().gv_transport(self.handle, ctypes.byref(t), _ptr(node0), _ptr(node_material), _ptr(sigma_n),
-                                 int(sigma_n.numel() // 2), _ptr(xi), int(kmax), ctypes.byref(o),
+                                 int(sigma_n.numel() // 2), _ptr(xi), int(kmax), PRECISIONS[precision], ctypes.byref(o),
                                  _stream_ptr(stream)))
         return out
 

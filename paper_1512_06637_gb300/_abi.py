@@ -92,7 +92,7 @@ SIGNATURES = {
     "gv_nav_locate": (_i, [_p, ctypes.POINTER(Tracks), _p, _p]),
     "gv_nav_step": (_i, [_p, ctypes.POINTER(Tracks), _p, _i, _p, _p, _p, _p, _p]),
     "gv_transport": (_i, [_p, ctypes.POINTER(Tracks), _p, _p, _p, ctypes.c_int32, _p, ctypes.c_int32,
-                          ctypes.POINTER(TransportOut), _p]),
+                          ctypes.c_int, ctypes.POINTER(TransportOut), _p]),
     "gv_server_create": (_i, [_p, ctypes.POINTER(ServerConfig), _p]),
     "gv_server_submit": (_i, [_p, _i64, _p, _p, _p]),
     "gv_server_poll": (_i, [_p, _i64, _p]),

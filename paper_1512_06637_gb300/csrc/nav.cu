@@ -690,6 +690,124 @@ __device__ inline void nav_one64(const NodeD* __restrict__ nodes, const int32_t*
   second = runner;
 }
 
+// The binary32 track of a binary64 point and direction, split as the bulk pass splits its
+// inputs (world frame: no frame error yet).
+__device__ __forceinline__ f32::TrackF track_from(const double p[3], const double d[3]) {
+  auto bits = [](double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return make_uint2((unsigned)b, (unsigned)(b >> 32));
+  };
+  f32::TrackF T;
+  T.bad = false;
+  T.fl = f32::FLOOR;
+  T.dfl = 0.f;
+  T.keyed = false;
+  T.zkey = 0;
+  f32::split(bits(p[0]), T.xh, T.xl, T.bad);
+  f32::split(bits(p[1]), T.yh, T.yl, T.bad);
+  f32::split(bits(p[2]), T.zh, T.zl, T.bad);
+  T.u = f32::trunc_hi(bits(d[0]), T.bad);
+  T.v = f32::trunc_hi(bits(d[1]), T.bad);
+  T.w = f32::trunc_hi(bits(d[2]), T.bad);
+  bool unused = false;
+  float h;
+  f32::split(bits(d[0]), h, T.ul, unused);
+  f32::split(bits(d[1]), h, T.vl, unused);
+  f32::split(bits(d[2]), h, T.wl, unused);
+  return T;
+}
+
+// The geometry half of a step as nav_one64 gives it, with the candidates ranked in binary32
+// first: when the binary32 pass certifies the nearest boundary (its interval apart from every
+// other candidate's) and puts the runner-up beyond the near-tie margin, only that candidate
+// is evaluated in binary64.  Its binary64 distance is then the minimum nav_one64 finds (each
+// binary64 value lies in its candidate's interval), and the runner-up's lower bound gives the
+// same near-tie decision.  A node with a grid, a flagged query or a close runner-up goes to
+// nav_one64.
+__device__ __noinline__ void nav_one_rank32(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                      const Desc* __restrict__ solids, int32_t v, const double p[3], const double d[3],
+                                      double& step, int32_t& next, double& second, const Vox& vox) {
+  constexpr int kMother = 0x7ffffffe, kNone = 0x7fffffff;
+  const NodeD& N = nodes[v];
+  const f32::TrackF W = track_from(p, d);
+  bool ok = !W.bad && !(vox.grids && N.grid >= 0);
+  Top2<false> top{F_INF, 0.f, F_INF, 0.f, kNone, kNone};
+  if (ok) {
+    f32::R32 R;
+    query32(solids[N.desc], to_local32(N, W), f32::kWantDout, R);
+    ok = !R.flag && R.dout >= 0;
+    if (ok) top.add(R.dout, half_tol(R.dout), kMother);
+    for (int j = 0; ok && j < N.count; j++) {
+      const NodeD& C = nodes[children[N.first + j]];
+      query32(solids[C.desc], to_local32(C, W), f32::kWantDin, R);
+      if (R.flag) ok = false;
+      else if (R.din >= 0) top.add(R.din, half_tol(R.din), j);
+    }
+    ok = ok && isfinite(top.b1) && top.b2 - top.e2 > top.b1 + top.e1;
+  }
+  if (ok) {
+    const bool mother = top.w1 == kMother;
+    const NodeD& M = mother ? N : nodes[children[N.first + top.w1]];
+    f64::Track T;
+    f64::Result R;
+    to_local64(M, p[0], p[1], p[2], T.x, T.y, T.z);
+    rot_local64(M, d[0], d[1], d[2], T.u, T.v, T.w);
+    query64(solids[M.desc], T, mother ? f64::kWantDout : f64::kWantDin, R);
+    const double t = mother ? R.dout : R.din;
+    const double lo2 = (double)top.b2 - (double)top.e2;  // the runner-up's lower bound
+    if (t >= 0 && lo2 - t > 2e-9 * (1.0 + t)) {
+      step = t;
+      next = mother ? -1 : children[N.first + top.w1];
+      second = lo2;
+      return;
+    }
+  }
+  nav_one64(nodes, children, solids, v, p, d, step, next, second, vox);
+}
+
+// Locate as locate64_surf, with the codes taken in binary32 when every one on the way is
+// certified (a certified code is the binary64 one); otherwise locate64_surf decides.
+__device__ __noinline__ int32_t locate_rank32(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
+                                        const Desc* __restrict__ solids, double x, double y, double z, bool& surf,
+                                        const Vox& vox) {
+  const double p[3] = {x, y, z}, d0[3] = {0.0, 0.0, 0.0};
+  const f32::TrackF W = track_from(p, d0);
+  if (!W.bad) {
+    bool sf = false;
+    f32::R32 R;
+    query32(solids[nodes[0].desc], to_local32(nodes[0], W), f32::kWantCode, R);
+    bool ok = !R.flag;
+    int32_t v = -1;
+    if (ok) {
+      sf |= R.code == 1;
+      if (R.code != 2) {
+        v = 0;
+        for (int depth = 0; ok && depth < 64; depth++) {
+          const NodeD& N = nodes[v];
+          int32_t into = -1;
+          const int32_t* ids;
+          int count;
+          candidates64(N, children, vox, x, y, z, ids, count);
+          for (int j = 0; j < count; j++) {
+            const int32_t c = ids[j];
+            query32(solids[nodes[c].desc], to_local32(nodes[c], W), f32::kWantCode, R);
+            if (R.flag) { ok = false; break; }
+            sf |= R.code == 1;
+            if (R.code != 2) { into = c; break; }
+          }
+          if (!ok || into < 0) break;
+          v = into;
+        }
+      }
+    }
+    if (ok) {
+      surf |= sf;
+      return v;
+    }
+  }
+  return locate64_surf(nodes, children, solids, x, y, z, surf, vox);
+}
+
 struct TransportArgs {
   const double *x, *y, *z, *u, *v, *w;  // start points and directions
   const int32_t* node0;                 // start volumes
@@ -697,6 +815,7 @@ struct TransportArgs {
   const double* sigma_n;                // n sigma of (scatter, absorb) per material, 1/mm
   const double* xi;                     // random numbers, [n][kmax][4], in (0, 1]
   int32_t kmax, nmat, nnodes;
+  int32_t rank32;                       // rank the step's candidates and the codes in binary32
   int8_t* reason;
   int32_t* steps;
   double *xo, *yo, *zo, *path;
@@ -737,7 +856,8 @@ __device__ inline void flight_step(const NodeD* __restrict__ nodes, const int32_
   const double* r = a.xi + ((size_t)i * (size_t)a.kmax + (size_t)F.k) * 4;
   double dgeo, second;
   int32_t next;
-  nav_one64(nodes, children, solids, F.v, F.p, F.d, dgeo, next, second, vox);
+  if (a.rank32) nav_one_rank32(nodes, children, solids, F.v, F.p, F.d, dgeo, next, second, vox);
+  else nav_one64(nodes, children, solids, F.v, F.p, F.d, dgeo, next, second, vox);
   const int32_t m = a.material[F.v];
   if (dgeo < 0 || m < 0 || m >= a.nmat) { F.why = GV_LOST; F.live = false; return; }
   const double sig0 = a.sigma_n[2 * m], sig1 = a.sigma_n[2 * m + 1];
@@ -772,8 +892,10 @@ __device__ inline void flight_locate(const NodeD* __restrict__ nodes, const int3
                                      const Vox& vox) {
   bool surf = false;
   F.reloc = false;
-  F.v = locate64_surf(nodes, children, solids, xadd(F.p[0], xmul(kPush, F.d[0])), xadd(F.p[1], xmul(kPush, F.d[1])),
-                      xadd(F.p[2], xmul(kPush, F.d[2])), surf, vox);
+  const double q0 = xadd(F.p[0], xmul(kPush, F.d[0])), q1 = xadd(F.p[1], xmul(kPush, F.d[1])),
+               q2 = xadd(F.p[2], xmul(kPush, F.d[2]));
+  F.v = a.rank32 ? locate_rank32(nodes, children, solids, q0, q1, q2, surf, vox)
+                 : locate64_surf(nodes, children, solids, q0, q1, q2, surf, vox);
   F.near |= surf;
   if (F.v < 0) { F.why = GV_ESCAPED; F.live = false; return; }
   if (F.k >= a.kmax) F.live = false;  // truncated
@@ -1138,11 +1260,12 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
 }
 
 gv_status gv_transport(const gv_geom* g, const gv_tracks* t, const int32_t* node0, const int32_t* node_material,
-                       const double* sigma_n, int32_t nmat, const double* xi, int32_t kmax,
+                       const double* sigma_n, int32_t nmat, const double* xi, int32_t kmax, gv_precision prec,
                        const gv_transport_out* out, void* stream) {
   if (!g || !t || !out) return set_error(GV_ERR_INVALID_ARG, "transport: NULL geometry, tracks or outputs");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "transport: negative track count");
   if (kmax < 1 || nmat < 1) return set_error(GV_ERR_INVALID_ARG, "transport: kmax and nmat must be >= 1");
+  if (prec != GV_FP64 && prec != GV_FP32_REFINE) return set_error(GV_ERR_INVALID_ARG, "unknown precision");
   if (t->n == 0) return GV_OK;
   if (!t->x || !t->y || !t->z || !t->dx || !t->dy || !t->dz || !node0 || !node_material || !sigma_n || !xi ||
       !out->reason || !out->steps || !out->x || !out->y || !out->z || !out->path || !out->last || !out->tie)
@@ -1152,7 +1275,7 @@ gv_status gv_transport(const gv_geom* g, const gv_tracks* t, const int32_t* node
     if ((uintptr_t)ptrs[i] & 7u) return set_error(GV_ERR_INVALID_ARG, "transport: arrays must be 8-byte aligned");
   if ((uintptr_t)out->z & 7u) return set_error(GV_ERR_INVALID_ARG, "transport: arrays must be 8-byte aligned");
   TransportArgs a{t->x, t->y, t->z, t->dx, t->dy, t->dz, node0, node_material, sigma_n, xi, kmax, nmat, g->nnodes,
-                  out->reason, out->steps, out->x, out->y, out->z, out->path, out->last, out->tie, t->n};
+                  prec == GV_FP32_REFINE ? 1 : 0, out->reason, out->steps, out->x, out->y, out->z, out->path, out->last, out->tie, t->n};
   // Resident blocks only: each block owns a contiguous range of tracks and keeps its pool
   // full from it, so it drains (slots empty while its last tracks finish) once per range.
   static int resident = 0;

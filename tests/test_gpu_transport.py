@@ -88,3 +88,31 @@ def test_transport_edges(gv, geo):
     got, _ = run_both(gv, geo, tr, node0, bad, np.zeros((1, 2)), xi, 16, with_oracle=False)
     inside = node0 >= 0
     assert (got["reason"][inside] == 3).all()
+
+
+@pytest.mark.parametrize("which", ["nested", "crowded"])
+def test_transport_rank32_same_bits(gv, which):
+    """Ranking the step's candidates and the relocation's codes in binary32 first changes no
+    bit of the results: the binary32 pass only decides which candidate binary64 evaluates."""
+    import torch
+    geo = W.nested_geometry() if which == "nested" else W.crowded_geometry()
+    n, kmax = 30011, 32
+    tr = W.nested_tracks(n, seed=77, geom=geo) if which == "nested" else W.crowded_tracks(geo, n, seed=77, surf_frac=0.1)
+    m = W.transport_materials(geo) if which == "nested" else W.crowded_materials(geo)
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    dev = to_device(tr, torch)
+    node0 = G.locate(dev)
+    args = (node0, torch.from_numpy(m["node_material"]).cuda(),
+            torch.from_numpy(np.ascontiguousarray(m["sigma_n"], np.float64)).cuda(),
+            torch.from_numpy(W.transport_xi(n, kmax, seed=77)).cuda(), kmax)
+    res = {}
+    for prec in ("fp64", "fp32_refine"):
+        for vox in (True, False):
+            G.set_voxels(vox)
+            o = G.transport(dev, *args, precision=prec)
+            torch.cuda.synchronize()
+            res[prec, vox] = {k: v.cpu().numpy() for k, v in o.items()}
+    ref = res["fp64", True]
+    for key, r in res.items():
+        for k in ref:
+            assert np.array_equal(r[k], ref[k]), (which, key, k)
