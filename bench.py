@@ -764,7 +764,8 @@ def run_batched_only(args):
 
 
 def run_transport_only(args, n=1 << 17, kmax=64):
-    """The transport loop alone (for profiling): nested detector, 2^17 tracks, kmax 64."""
+    """The transport loop alone (for profiling): nested detector, 2^17 tracks, kmax 64;
+    --precision fp32_refine ranks the candidates in binary32 first (auto: binary64)."""
     import torch
     import paper_1512_06637_gb300 as gv
     geo = W.nested_geometry()
@@ -775,12 +776,14 @@ def run_transport_only(args, n=1 << 17, kmax=64):
     mat = torch.from_numpy(m["node_material"]).cuda()
     sig = torch.from_numpy(m["sigma_n"]).cuda()
     xi = torch.from_numpy(W.transport_xi(n, kmax, seed=1)).cuda()
-    out = G.transport(dev, node0, mat, sig, xi, kmax)
+    prec = "fp32_refine" if args.precision == "fp32_refine" else "fp64"
+    out = G.transport(dev, node0, mat, sig, xi, kmax, precision=prec)
     for _ in range(args.warmup):
-        G.transport(dev, node0, mat, sig, xi, kmax, out=out)
-    ms = _timed(torch, lambda: G.transport(dev, node0, mat, sig, xi, kmax, out=out), max(1, args.steps))
+        G.transport(dev, node0, mat, sig, xi, kmax, out=out, precision=prec)
+    ms = _timed(torch, lambda: G.transport(dev, node0, mat, sig, xi, kmax, out=out, precision=prec), max(1, args.steps))
     steps = int(out["steps"].sum().item())
-    print(json.dumps({"form": "transport", "tracks": n, "ms": ms, "steps_per_s": steps / (ms * 1e-3)}), flush=True)
+    print(json.dumps({"form": "transport", "precision": prec, "tracks": n, "ms": ms,
+                      "steps_per_s": steps / (ms * 1e-3)}), flush=True)
 
 
 def main():
