@@ -661,7 +661,9 @@ def bench_voxels(gv, torch, reps=3, n=1 << 20, n_transport=1 << 18, kmax=32):
                                                                   safety=False), r),
             "fp32_refine_step_nosafety_ms": _timed(torch, lambda: G.step(dev, node, precision="fp32_refine",
                                                                          workspace=ws, out=out, safety=False), r),
-            "transport_ms": _timed(torch, lambda: G.transport(tdev, node0, mat, sig, xi, kmax, out=tout), r)}
+            "transport_ms": _timed(torch, lambda: G.transport(tdev, node0, mat, sig, xi, kmax, out=tout), r),
+            "transport_rank32_ms": _timed(torch, lambda: G.transport(tdev, node0, mat, sig, xi, kmax, out=tout,
+                                                                     precision="fp32_refine"), r)}
         res[key]["fp64_steps_per_s"] = n / (res[key]["fp64_step_ms"] * 1e-3)
         res[key]["transport_steps_per_s"] = int(tout["steps"].sum().item()) / (res[key]["transport_ms"] * 1e-3)
     G.set_voxels(True)
