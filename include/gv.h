@@ -153,7 +153,7 @@ gv_status gv_query(const gv_solid* s, const gv_tracks* tracks, gv_precision prec
  * and chunk c-1 copied out, so the host link carries both directions at once and
  * the kernels run under the copies.  Host arrays should be pinned
  * (cudaHostAlloc/cudaHostRegister); pageable memory gives the same results, with
- * copies staged by the driver that do not overlap.  The paper's baskets are
+ * copies staged through the CUDA runtime that do not overlap.  The paper's baskets are
  * filled on the host by the scheduler (Project goals, item 1); this is how they
  * reach the device. */
 typedef struct gv_pipeline gv_pipeline;
