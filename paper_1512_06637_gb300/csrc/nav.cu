@@ -170,15 +170,6 @@ __device__ inline int32_t locate64(const NodeD* __restrict__ nodes, const int32_
   return v;
 }
 
-__global__ void __launch_bounds__(256, 2) k_locate(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                                const Desc* __restrict__ solids, const double* __restrict__ x,
-                                                const double* __restrict__ y, const double* __restrict__ z,
-                                                int32_t* __restrict__ out, int64_t n, Vox vox) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    out[i] = locate64(nodes, children, solids, x[i], y[i], z[i], vox);
-}
-
 struct NavArgs {
   const double *x, *y, *z, *u, *v, *w;
   const int32_t* node;
@@ -808,6 +799,19 @@ __device__ __noinline__ int32_t locate_rank32(const NodeD* __restrict__ nodes, c
   return locate64_surf(nodes, children, solids, x, y, z, surf, vox);
 }
 
+// Locate with the codes ranked in binary32 first (the same nodes as k_locate).
+__global__ void __launch_bounds__(256, 2) k_locate32(const NodeD* __restrict__ nodes,
+                                                  const int32_t* __restrict__ children,
+                                                  const Desc* __restrict__ solids, const double* __restrict__ x,
+                                                  const double* __restrict__ y, const double* __restrict__ z,
+                                                  int32_t* __restrict__ out, int64_t n, Vox vox) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    bool surf = false;
+    out[i] = locate_rank32(nodes, children, solids, x[i], y[i], z[i], surf, vox);
+  }
+}
+
 struct TransportArgs {
   const double *x, *y, *z, *u, *v, *w;  // start points and directions
   const int32_t* node0;                 // start volumes
@@ -1215,8 +1219,8 @@ gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* t, int32_t* node, voi
   if (t->n == 0) return GV_OK;
   if (!t->x || !t->y || !t->z || !node) return set_error(GV_ERR_INVALID_ARG, "locate: NULL array");
   int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sm_count() * 8);
-  k_locate<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, t->x, t->y,
-                                                                 t->z, node, t->n, vox_of(g));
+  k_locate32<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g->d_nodes, g->d_children, g->d_solids, t->x, t->y,
+                                                                   t->z, node, t->n, vox_of(g));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GV_OK : cuda_error(e, "locate launch");
 }
