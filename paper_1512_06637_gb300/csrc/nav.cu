@@ -143,33 +143,6 @@ __device__ __forceinline__ void candidates64(const NodeD& N, const int32_t* __re
   count = vox.cells[2 * cell + 1] - vox.cells[2 * cell];
 }
 
-__device__ inline int32_t locate64(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
-                                   const Desc* __restrict__ solids, double x, double y, double z,
-                                   const Vox& vox = Vox{nullptr, nullptr, nullptr}) {
-  f64::Track T{0, 0, 0, 0, 0, 0};
-  f64::Result R;
-  to_local64(nodes[0], x, y, z, T.x, T.y, T.z);
-  query64(solids[nodes[0].desc], T, f64::kWantCode, R);
-  if (R.code == 2) return -1;
-  int32_t v = 0;
-  for (int depth = 0; depth < 64; depth++) {
-    const NodeD& N = nodes[v];
-    int32_t into = -1;
-    const int32_t* ids;
-    int count;
-    candidates64(N, children, vox, x, y, z, ids, count);
-    for (int j = 0; j < count; j++) {
-      const int32_t c = ids[j];
-      to_local64(nodes[c], x, y, z, T.x, T.y, T.z);
-      query64(solids[nodes[c].desc], T, f64::kWantCode, R);
-      if (R.code != 2) { into = c; break; }
-    }
-    if (into < 0) break;
-    v = into;
-  }
-  return v;
-}
-
 struct NavArgs {
   const double *x, *y, *z, *u, *v, *w;
   const int32_t* node;
@@ -610,8 +583,10 @@ __global__ void __launch_bounds__(256, 2) k_nav_fp32(const NodeD* __restrict__ n
 
 // ------------------------------------------------------------ transport loop
 
-// Locate one point (as locate64) and report whether any classification on the way was
-// SURFACE (the point lies on a boundary within the tolerance).
+// Locate one point in binary64 (gv_nav_locate's definition: from the world down, enter
+// the first daughter, in index order or in the point's grid cell, that does not classify
+// the point OUTSIDE; -1 outside the world) and report whether any classification on the
+// way was SURFACE (the point lies on a boundary within the tolerance).
 __device__ inline int32_t locate64_surf(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                         const Desc* __restrict__ solids, double x, double y, double z, bool& surf,
                                         const Vox& vox) {
