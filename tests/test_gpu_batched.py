@@ -1,5 +1,5 @@
-"""Batched evaluation (many baskets, each against its own solid, one persistent
-launch replayed from a CUDA graph), checked against the CPU oracle.
+"""Batched evaluation (many baskets, each against its own solid, persistent kernels per
+solid family replayed from one CUDA graph), checked against the CPU oracle.
 
 The full batched workload (4096 baskets of 16-4096 tracks over 64 solids of the
 six types) is small enough for the oracle to check every track.  Also: results
