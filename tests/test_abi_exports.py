@@ -62,3 +62,19 @@ def test_invalid_solids_rejected_on_host(libpath):
     assert lib.gv_solid_trap(bad_trap, ctypes.byref(h)) == _abi.GV_ERR_INVALID_ARG
     assert b"planar" in lib.gv_last_error()
     assert lib.gv_query(None, None, 0, None, None, None) == _abi.GV_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_header_is_plain_c(lang, tmp_path):
+    """include/gv.h compiles on its own as strict C99 and as C++17 (no torch or CUDA types)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("t.c" if lang == "c" else "t.cpp")
+    src.write_text('#include "gv.h"\nint main(void) { gv_status s = GV_OK; (void)s; return 0; }\n')
+    std = "-std=c99" if lang == "c" else "-std=c++17"
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
