@@ -19,17 +19,19 @@
  *             (polycone: per-section closed constraint sets, see below).
  *
  *   Distance: every root t > 0 of every constraint surface along p + t d is a
- *   candidate; the gaps between consecutive candidates are classified inside or
- *   outside by the sign of s at their midpoint (no tolerance).
+ *   candidate (roots closer than 1e-12 mm merged); the gaps between consecutive
+ *   candidates are classified inside or outside by the sign of s at their
+ *   midpoint (no tolerance).
  *   DistanceToIn:  INSIDE -> -1; SURFACE and entering -> 0; otherwise the first
  *                  candidate where an outside gap is followed by an inside one;
  *                  none -> +inf.
- *   DistanceToOut: OUTSIDE -> -1; SURFACE and leaving -> 0; otherwise the first
- *                  candidate where an inside gap is followed by an outside one;
- *                  none (a surface point whose ray never gets inside) -> 0.
- *   A SURFACE point is "leaving" when some constraint within the band
- *   (g_i >= -h) grows along d, and "entering" when every such constraint
- *   decreases along d.
+ *   DistanceToOut: OUTSIDE -> -1; SURFACE and not entering -> 0; otherwise the
+ *                  first candidate where an inside gap is followed by an outside
+ *                  one; none (a surface point whose ray never gets inside) -> 0.
+ *   A SURFACE point is "entering" when every constraint within the band
+ *   (g_i >= -h) shrinks along d.  Rays that graze or run along a surface follow
+ *   the readings stated above the surface-start code below (tangent, sliding,
+ *   touch).
  */
 #include "gv_oracle.h"
 #include <math.h>
@@ -336,72 +338,195 @@ double or_safety_out(const or_solid* s, const double p[3]) {
   return -s_closed(s, section_of(s, p[2]), p);
 }
 
-/* ------------------------------------------- surface start: in or out? */
+/* ------------------------------------------- rays along and across surfaces */
 
-/* Over the constraints of s at p that lie within the band (g >= -h): does any
- * grow along d (leaving), and does every one shrink along d (entering)? */
-static void surface_motion(const or_solid* s, const double p[3], const double d[3],
-                           int* leaving, int* entering);
+/* Readings for rays that meet a surface at a grazing angle (the paper gives none):
+ *
+ * Tangent.  The derivative along d of a constraint that holds the start point within the
+ * band is taken per unit length (plane and phi normals are unit vectors, a lateral wall
+ * r = a z + b gives (d r/dt - a d_z) k).  Within OR_TAU of zero it is tangent: a tangent
+ * plane is one the ray runs along; a tangent wall curves away from the ray unless the ray
+ * lies in the meridian plane of the point (|p_xy x d_xy| <= OR_TAU r), where it runs along
+ * a straight generator of the wall.  A convex (outer) wall that curves away is left, a
+ * concave (inner) one is entered.
+ *
+ * Sliding.  A constraint within the band whose surface the ray runs along (a tangent
+ * plane, or a wall along its generator) slides: along the ray the point stays on that
+ * surface, which is the boundary and not the interior.  It has no crossing of its own,
+ * and its value along the ray is taken as violated (+inf; -inf for the subtracted solid
+ * of a boolean subtraction, whose complement it bounds).
+ *
+ * Surface start.  A point on the surface enters when every constraint within the band
+ * shrinks along d (tangent concave walls included); otherwise the ray does not get into
+ * the interior at 0+, and DistanceToOut is 0.
+ *
+ * Touch.  A wall crossed where the quadratic's discriminant is within its rounding bound
+ * of zero is touched (a double root): no crossing.  Crossings closer
+ * than OR_MERGE mm are one crossing: a chord shorter than that is a touch. */
+#define OR_TAU 1e-12
+#define OR_MERGE 1e-12
+#define OR_DISC (16 * 1.1102230246251565e-16)
 
-/* A boolean surface point: over the components within the band |s_x| <= h, each with its
- * own motion (the complement of c, for a subtraction, with entering and leaving swapped):
- * a union is entered when some band component is entered and left when all are left; an
- * intersection (and a subtraction, a n not-c) is entered when all are entered and left
- * when some is left. */
-static void bool_motion(const or_bool* b, const double p[3], const double d[3], int* leaving, int* entering) {
-  double pc[3], dc[3];
-  bool_to_c(b, p, d, pc, dc);
-  const double sa = or_s_code(&b->a, p), sc = or_s_code(&b->c, pc);
-  int la = 0, ea = 0, lc = 0, ec = 0;
-  const int ba = fabs(sa) <= H, bc = fabs(sc) <= H;
-  if (ba) surface_motion(&b->a, p, d, &la, &ea);
-  if (bc) surface_motion(&b->c, pc, dc, &lc, &ec);
-  if (b->op == OR_SUBTRACTION) { const int tmp = lc; lc = ec; ec = tmp; }
-  if (b->op == OR_UNION) {
-    *entering = (ba && ea) || (bc && ec);
-    *leaving = (!ba || la) && (!bc || lc);
+enum { SL_OUT = 1, SL_IN = 2, SL_Z0 = 4, SL_ZL = 8, SL_PS = 16, SL_PE = 32 };
+
+/* The sliding constraints of one primitive along one ray. */
+typedef struct {
+  unsigned bits;  /* planar: bit i = plane i; polycone family: SL_* */
+  int k0;         /* polycone family: the start point's section (its walls slide) */
+  double forced;  /* the value a sliding constraint takes along the ray */
+} slide1;
+
+typedef struct { slide1 a, c; } or_slide;  /* a primitive uses a; a boolean a and c */
+
+/* One constraint at the start point: value, derivative per unit length along d, motion
+ * (+1 grows, -1 shrinks, 0 runs along its surface), sliding bit, and whether it takes
+ * part in the surface-start rule (a wide phi uses the plane holding the smaller value). */
+typedef struct { double g, gd; int m; unsigned bit; int motion; } cons;
+
+static int plane_motion(double gd) { return gd > OR_TAU ? 1 : (gd < -OR_TAU ? -1 : 0); }
+
+static double wall_gd(const or_line* L, const double p[3], const double d[3], double r) {
+  const double rd = r > 0 ? (p[0] * d[0] + p[1] * d[1]) / r : sqrt(d[0] * d[0] + d[1] * d[1]);
+  return (rd - L->a * d[2]) * L->k;
+}
+
+static int wall_motion(double gd, const double p[3], const double d[3], double r, int outer) {
+  if (gd > OR_TAU) return 1;
+  if (gd < -OR_TAU) return -1;
+  if (r > 0 && fabs(p[0] * d[1] - p[1] * d[0]) > OR_TAU * r) return outer ? 1 : -1;
+  return 0;
+}
+
+/* The constraints of a primitive at its start point p along d. */
+static int start_constraints(const or_solid* s, const double p[3], const double d[3], cons* c, int* k0) {
+  int m = 0;
+  *k0 = 0;
+  if (s->family == 0) {
+    for (int i = 0; i < s->nplanes; i++) {
+      c[m].g = plane_g(&s->pl[i], p);
+      c[m].gd = dot3(s->pl[i].n, d);
+      c[m].m = plane_motion(c[m].gd);
+      c[m].bit = 1u << i;
+      c[m].motion = 1;
+      m++;
+    }
+    return m;
+  }
+  const double r = rho(p), z = p[2];
+  const int k = section_of(s, z);
+  *k0 = k;
+  c[m].g = line_out_g(&s->out[k], r, z);
+  c[m].gd = wall_gd(&s->out[k], p, d, r);
+  c[m].m = wall_motion(c[m].gd, p, d, r, 1);
+  c[m].bit = SL_OUT; c[m].motion = 1; m++;
+  if (s->in[k].present) {
+    c[m].g = line_in_g(&s->in[k], r, z);
+    c[m].gd = -wall_gd(&s->in[k], p, d, r);
+    c[m].m = wall_motion(c[m].gd, p, d, r, 0);
+    c[m].bit = SL_IN; c[m].motion = 1; m++;
+  }
+  c[m].g = s->z[0] - z; c[m].gd = -d[2]; c[m].m = plane_motion(c[m].gd); c[m].bit = SL_Z0; c[m].motion = 1; m++;
+  c[m].g = z - s->z[s->nz - 1]; c[m].gd = d[2]; c[m].m = plane_motion(c[m].gd); c[m].bit = SL_ZL; c[m].motion = 1; m++;
+  if (s->has_phi) {
+    const double a = phi_plane(s->ns, p), b = phi_plane(s->ne, p);
+    c[m].g = a; c[m].gd = phi_plane(s->ns, d); c[m].m = plane_motion(c[m].gd); c[m].bit = SL_PS;
+    c[m].motion = !s->phi_wide || a <= b; m++;
+    c[m].g = b; c[m].gd = phi_plane(s->ne, d); c[m].m = plane_motion(c[m].gd); c[m].bit = SL_PE;
+    c[m].motion = !s->phi_wide || !(a <= b); m++;
+  }
+  return m;
+}
+
+static void slide_setup1(const or_solid* s, const double p[3], const double d[3], double forced, slide1* sl) {
+  cons c[8];
+  int k0;
+  const int m = start_constraints(s, p, d, c, &k0);
+  sl->bits = 0;
+  sl->k0 = k0;
+  sl->forced = forced;
+  for (int i = 0; i < m; i++)
+    if (fabs(c[i].g) <= H && c[i].m == 0) sl->bits |= c[i].bit;
+}
+
+static void slide_setup(const or_solid* s, const double p[3], const double d[3], or_slide* sl) {
+  if (s->type == OR_BOOL) {
+    double pc[3], dc[3];
+    bool_to_c(s->bl, p, d, pc, dc);
+    slide_setup1(&s->bl->a, p, d, INFINITY, &sl->a);
+    slide_setup1(&s->bl->c, pc, dc, s->bl->op == OR_SUBTRACTION ? -INFINITY : INFINITY, &sl->c);
   } else {
-    *entering = (!ba || ea) && (!bc || ec);
-    *leaving = (ba && la) || (bc && lc);
+    slide_setup1(s, p, d, INFINITY, &sl->a);
   }
 }
 
-static void surface_motion(const or_solid* s, const double p[3], const double d[3],
-                           int* leaving, int* entering) {
-  if (s->type == OR_BOOL) { bool_motion(s->bl, p, d, leaving, entering); return; }
-  double g[8], gd[8];
-  int m = 0;
+/* The decision quantity at q along a ray, sliding constraints at their forced value. */
+static double s_ray1(const or_solid* s, const double q[3], const slide1* sl) {
   if (s->family == 0) {
-    for (int i = 0; i < s->nplanes; i++) { g[m] = plane_g(&s->pl[i], p); gd[m] = dot3(s->pl[i].n, d); m++; }
-  } else {
-    const double r = rho(p), z = p[2];
-    const int k = section_of(s, z);
-    const double radial = p[0] * d[0] + p[1] * d[1];
-    g[m] = line_out_g(&s->out[k], r, z); gd[m] = radial - s->out[k].a * d[2] * r; m++;
-    if (s->in[k].present) { g[m] = line_in_g(&s->in[k], r, z); gd[m] = -(radial - s->in[k].a * d[2] * r); m++; }
-    g[m] = s->z[0] - z; gd[m] = -d[2]; m++;
-    g[m] = z - s->z[s->nz - 1]; gd[m] = d[2]; m++;
-    if (s->has_phi) {
-      const double a = phi_plane(s->ns, p), b = phi_plane(s->ne, p);
-      const double ad = phi_plane(s->ns, d), bd = phi_plane(s->ne, d);
-      if (s->phi_wide) {
-        if (a <= b) { g[m] = a; gd[m] = ad; } else { g[m] = b; gd[m] = bd; }
-        m++;
-      } else {
-        g[m] = a; gd[m] = ad; m++;
-        g[m] = b; gd[m] = bd; m++;
-      }
+    double v = -INFINITY;
+    for (int i = 0; i < s->nplanes; i++)
+      v = dmax(v, (sl->bits >> i) & 1u ? sl->forced : plane_g(&s->pl[i], q));
+    return v;
+  }
+  const double r = rho(q), z = q[2];
+  const int k = section_of(s, z);
+  const int own = k == sl->k0;
+  double v = own && (sl->bits & SL_OUT) ? sl->forced : line_out_g(&s->out[k], r, z);
+  v = dmax(v, sl->bits & SL_Z0 ? sl->forced : s->z[0] - z);
+  v = dmax(v, sl->bits & SL_ZL ? sl->forced : z - s->z[s->nz - 1]);
+  if (s->in[k].present) v = dmax(v, own && (sl->bits & SL_IN) ? sl->forced : line_in_g(&s->in[k], r, z));
+  if (s->has_phi) {
+    const double a = sl->bits & SL_PS ? sl->forced : phi_plane(s->ns, q);
+    const double b = sl->bits & SL_PE ? sl->forced : phi_plane(s->ne, q);
+    v = dmax(v, s->phi_wide ? dmin(a, b) : dmax(a, b));
+  }
+  return v;
+}
+
+static double s_ray(const or_solid* s, const double q[3], const or_slide* sl) {
+  if (s->type != OR_BOOL) return s_ray1(s, q, &sl->a);
+  double qc[3];
+  bool_to_c(s->bl, q, NULL, qc, NULL);
+  return bool_combine(s->bl->op, s_ray1(&s->bl->a, q, &sl->a), s_ray1(&s->bl->c, qc, &sl->c));
+}
+
+/* ------------------------------------------- surface start: does the ray enter? */
+
+static int entering_of(const or_solid* s, const double p[3], const double d[3]);
+
+/* A boolean surface point: over the components within the band |s_x| <= h, each with its
+ * own rule (the complement of c, for a subtraction, is entered where c is certainly left:
+ * some constraint of c within the band grows): a union is entered when some band component
+ * is entered; an intersection (and a subtraction, a n not-c) when every band component is. */
+static int bool_entering(const or_bool* b, const double p[3], const double d[3]) {
+  double pc[3], dc[3];
+  bool_to_c(b, p, d, pc, dc);
+  const double sa = or_s_code(&b->a, p), sc = or_s_code(&b->c, pc);
+  const int ba = fabs(sa) <= H, bc = fabs(sc) <= H;
+  const int ea = ba && entering_of(&b->a, p, d);
+  int ec = 0;
+  if (bc) {
+    if (b->op == OR_SUBTRACTION) {
+      cons c[8];
+      int k0;
+      const int m = start_constraints(&b->c, pc, dc, c, &k0);
+      for (int i = 0; i < m; i++)
+        if (c[i].motion && c[i].g >= -H && c[i].m == 1) ec = 1;
+    } else {
+      ec = entering_of(&b->c, pc, dc);
     }
   }
-  int any_out = 0, all_in = 1;
-  for (int i = 0; i < m; i++) {
-    if (g[i] >= -H) {
-      if (gd[i] > 0) any_out = 1;
-      if (!(gd[i] < 0)) all_in = 0;
-    }
-  }
-  *leaving = any_out;
-  *entering = all_in;
+  if (b->op == OR_UNION) return (ba && ea) || (bc && ec);
+  return (!ba || ea) && (!bc || ec);
+}
+
+static int entering_of(const or_solid* s, const double p[3], const double d[3]) {
+  if (s->type == OR_BOOL) return bool_entering(s->bl, p, d);
+  cons c[8];
+  int k0;
+  const int m = start_constraints(s, p, d, c, &k0);
+  for (int i = 0; i < m; i++)
+    if (c[i].motion && c[i].g >= -H && c[i].m != -1) return 0;
+  return 1;
 }
 
 /* ------------------------------------------------- candidate crossings */
@@ -411,18 +536,23 @@ static void add_root(double* t, int* m, double v) {
 }
 
 /* Crossings of the surface r = a z + b (a z + b >= 0) by p + t d: the roots of
- * A t^2 + 2 B t + C = 0, by the cancellation-free pair q/A, C/q. */
+ * A t^2 + 2 B t + C = 0, by the cancellation-free pair q/A, C/q.  A discriminant within
+ * its rounding bound, OR_DISC (|B| Bs + |A| Cs + |C| As) with As, Bs, Cs the magnitudes of
+ * the terms A, B, C are formed from, is a double root (a touch, no crossing). */
 static void cone_roots(const or_line* L, const double p[3], const double d[3], double* t, int* m) {
   const double P = L->a * p[2] + L->b, D = L->a * d[2];
-  const double A = (d[0] * d[0] + d[1] * d[1]) - D * D;
+  const double A0 = d[0] * d[0] + d[1] * d[1], R2 = p[0] * p[0] + p[1] * p[1];
+  const double A = A0 - D * D;
   const double B = (p[0] * d[0] + p[1] * d[1]) - P * D;
-  const double C = (p[0] * p[0] + p[1] * p[1]) - P * P;
+  const double C = R2 - P * P;
   double r[2]; int nr = 0;
   if (A == 0) {
     if (B != 0) r[nr++] = -C / (2 * B);
   } else {
     const double disc = B * B - A * C;
-    if (disc > 0) {
+    const double As = A0 + D * D, Cs = R2 + P * P;
+    const double Bs = (fabs(p[0] * d[0]) + fabs(p[1] * d[1])) + fabs(P * D);
+    if (disc > OR_DISC * ((fabs(B) * Bs + fabs(A) * Cs) + fabs(C) * As)) {
       const double sq = sqrt(disc);
       const double q = -(B + (B >= 0 ? sq : -sq));
       r[nr++] = q / A;
@@ -446,57 +576,72 @@ static int cmp_double(const void* a, const void* b) {
   return x < y ? -1 : (x > y ? 1 : 0);
 }
 
-static int candidates(const or_solid* s, const double p[3], const double d[3], double* t) {
+/* Every crossing of a primitive's constraint surfaces except those of its sliding ones. */
+static int prim_roots(const or_solid* s, const double p[3], const double d[3], const slide1* sl, double* t) {
   int m = 0;
+  if (s->family == 0) {
+    for (int i = 0; i < s->nplanes; i++)
+      if (!((sl->bits >> i) & 1u)) plane_root(s->pl[i].n, s->pl[i].c, p, d, t, &m);
+    return m;
+  }
+  for (int k = 0; k + 1 < s->nz; k++) {
+    const int own = k == sl->k0;
+    if (!(own && (sl->bits & SL_OUT))) cone_roots(&s->out[k], p, d, t, &m);
+    if (s->in[k].present && !(own && (sl->bits & SL_IN))) cone_roots(&s->in[k], p, d, t, &m);
+  }
+  const double ez[3] = {0, 0, 1};
+  for (int k = 0; k < s->nz; k++) {
+    if (k == 0 && (sl->bits & SL_Z0)) continue;
+    if (k == s->nz - 1 && (sl->bits & SL_ZL)) continue;
+    plane_root(ez, s->z[k], p, d, t, &m);
+  }
+  if (s->has_phi) {
+    const double n1[3] = {s->ns[0], s->ns[1], 0}, n2[3] = {s->ne[0], s->ne[1], 0};
+    if (!(sl->bits & SL_PS)) plane_root(n1, 0, p, d, t, &m);
+    if (!(sl->bits & SL_PE)) plane_root(n2, 0, p, d, t, &m);
+  }
+  return m;
+}
+
+/* The crossings along the ray, sorted; crossings closer than OR_MERGE to the last one
+ * kept are merged into it. */
+static int candidates(const or_solid* s, const double p[3], const double d[3], const or_slide* sl, double* t) {
+  int m;
   if (s->type == OR_BOOL) {  /* every crossing of either component's surfaces */
     double pc[3], dc[3];
     bool_to_c(s->bl, p, d, pc, dc);
-    m = candidates(&s->bl->a, p, d, t);
-    m += candidates(&s->bl->c, pc, dc, t + m);
-  } else if (s->family == 0) {
-    for (int i = 0; i < s->nplanes; i++) plane_root(s->pl[i].n, s->pl[i].c, p, d, t, &m);
+    m = prim_roots(&s->bl->a, p, d, &sl->a, t);
+    m += prim_roots(&s->bl->c, pc, dc, &sl->c, t + m);
   } else {
-    for (int k = 0; k + 1 < s->nz; k++) {
-      cone_roots(&s->out[k], p, d, t, &m);
-      if (s->in[k].present) cone_roots(&s->in[k], p, d, t, &m);
-    }
-    const double ez[3] = {0, 0, 1};
-    for (int k = 0; k < s->nz; k++) plane_root(ez, s->z[k], p, d, t, &m);
-    if (s->has_phi) {
-      const double n1[3] = {s->ns[0], s->ns[1], 0}, n2[3] = {s->ne[0], s->ne[1], 0};
-      plane_root(n1, 0, p, d, t, &m);
-      plane_root(n2, 0, p, d, t, &m);
-    }
+    m = prim_roots(s, p, d, &sl->a, t);
   }
   qsort(t, (size_t)m, sizeof(double), cmp_double);
   int u = 0;
   for (int i = 0; i < m; i++)
-    if (u == 0 || t[i] != t[u - 1]) t[u++] = t[i];
+    if (u == 0 || t[i] - t[u - 1] > OR_MERGE) t[u++] = t[i];
   return u;
 }
 
 /* Inside (no tolerance) on the gap that follows candidate j-1 (gap 0 starts at t = 0). */
-static int gap_inside(const or_solid* s, const double p[3], const double d[3],
+static int gap_inside(const or_solid* s, const double p[3], const double d[3], const or_slide* sl,
                       const double* t, int m, int j) {
   const double lo = j == 0 ? 0.0 : t[j - 1];
   const double mid = j < m ? 0.5 * (lo + t[j]) : 2.0 * lo + 1.0;
   const double q[3] = {p[0] + mid * d[0], p[1] + mid * d[1], p[2] + mid * d[2]};
-  return or_s_code(s, q) <= 0;
+  return s_ray(s, q, sl) <= 0;
 }
 
 double or_dist_in(const or_solid* s, const double p[3], const double d[3]) {
   const int c = or_inside(s, p);
   if (c == OR_INSIDE) return -1.0;
-  if (c == OR_SURFACE) {
-    int leaving, entering;
-    surface_motion(s, p, d, &leaving, &entering);
-    if (entering) return 0.0;
-  }
+  if (c == OR_SURFACE && entering_of(s, p, d)) return 0.0;
+  or_slide sl;
+  slide_setup(s, p, d, &sl);
   double t[MAXROOTS];
-  const int m = candidates(s, p, d, t);
-  int prev = gap_inside(s, p, d, t, m, 0);
+  const int m = candidates(s, p, d, &sl, t);
+  int prev = gap_inside(s, p, d, &sl, t, m, 0);
   for (int j = 1; j <= m; j++) {
-    const int cur = gap_inside(s, p, d, t, m, j);
+    const int cur = gap_inside(s, p, d, &sl, t, m, j);
     if (cur && !prev) return t[j - 1];
     prev = cur;
   }
@@ -506,16 +651,14 @@ double or_dist_in(const or_solid* s, const double p[3], const double d[3]) {
 double or_dist_out(const or_solid* s, const double p[3], const double d[3]) {
   const int c = or_inside(s, p);
   if (c == OR_OUTSIDE) return -1.0;
-  if (c == OR_SURFACE) {
-    int leaving, entering;
-    surface_motion(s, p, d, &leaving, &entering);
-    if (leaving) return 0.0;
-  }
+  if (c == OR_SURFACE && !entering_of(s, p, d)) return 0.0;
+  or_slide sl;
+  slide_setup(s, p, d, &sl);
   double t[MAXROOTS];
-  const int m = candidates(s, p, d, t);
-  int prev = gap_inside(s, p, d, t, m, 0);
+  const int m = candidates(s, p, d, &sl, t);
+  int prev = gap_inside(s, p, d, &sl, t, m, 0);
   for (int j = 1; j <= m; j++) {
-    const int cur = gap_inside(s, p, d, t, m, j);
+    const int cur = gap_inside(s, p, d, &sl, t, m, j);
     if (!cur && prev) return t[j - 1];
     prev = cur;
   }

@@ -44,6 +44,19 @@ MUTANTS = {
     "boolean placement ignored": ("const double v[3] = {p[0] - b->t[0], p[1] - b->t[1], p[2] - b->t[2]};",
                                   "const double v[3] = {p[0], p[1], p[2]};"),
     "boolean union safety max": ("if (to_in) return dmin(sia, sic);", "if (to_in) return dmax(sia, sic);"),
+    "tangent threshold dropped": ("#define OR_TAU 1e-12", "#define OR_TAU 0.0"),
+    "tangent convex wall entered": ("return outer ? 1 : -1;", "return outer ? -1 : 1;"),
+    "generator ray taken as curved": ("if (r > 0 && fabs(p[0] * d[1] - p[1] * d[0]) > OR_TAU * r)", "if (r > 0)"),
+    "sliding surfaces not detected": ("if (fabs(c[i].g) <= H && c[i].m == 0) sl->bits |= c[i].bit;",
+                                      "if (0) sl->bits |= c[i].bit;"),
+    "sliding counted as inside": ("slide_setup1(s, p, d, INFINITY, &sl->a);", "slide_setup1(s, p, d, -INFINITY, &sl->a);"),
+    "subtracted face slide counted as outside c": ("s->bl->op == OR_SUBTRACTION ? -INFINITY : INFINITY", "INFINITY"),
+    "double root taken as a crossing": ("if (disc > OR_DISC * ((fabs(B) * Bs + fabs(A) * Cs) + fabs(C) * As))",
+                                        "if (disc > 0)"),
+    "crossings not merged": ("#define OR_MERGE 1e-12", "#define OR_MERGE 0.0"),
+    "surface start leaves only when a constraint grows": (
+        "if (c[i].motion && c[i].g >= -H && c[i].m != -1) return 0;",
+        "if (c[i].motion && c[i].g >= -H && c[i].m == 1) return 0;"),
     "boundary step shortened": ("for (int j = 0; j < 3; j++) p[j] = p[j] + dgeo * d[j];",
                                 "for (int j = 0; j < 3; j++) p[j] = p[j] + 0.5 * dgeo * d[j];"),
 }

@@ -364,6 +364,121 @@ def test_brute_force_ray_march(idx):
     assert agree_x.mean() >= 0.985, agree_x.mean()
 
 
+# ------------------------------------------------------------ grazing rays
+#
+# Rays that touch a surface, run along it, or pass exactly through an edge (the VecGeom
+# section's third question for the rays where it is hardest).  Each family is placed by
+# construction (workloads.grazing_tracks) and the answers are closed forms:
+#   * a ray tangent to a convex wall leaves it, to a concave wall enters the solid;
+#   * a ray running along a surface (a plane, a phi plane, a cone generator) stays on
+#     the boundary, which is not the interior: DistanceToOut 0 from the surface, and no
+#     entry through that surface;
+#   * a ray that touches an edge or a wall (a double root) does not enter.
+
+def _gq(fam, n, seed):
+    spec, tr, m = W.grazing_tracks(fam, n, seed)
+    return oracle.Solid.from_spec(spec).query(**tr), m
+
+
+def test_tangent_to_convex_wall_leaves():
+    """Tube (5, 20, 30, phi 0-270 deg), points on r = 20 (and within the band), directions
+    tangent to the wall: the ray is outside r = 20 for every t > 0."""
+    r, m = _gq("tube_outer_tangent", 3000, 31)
+    assert (r["inside"] == SURF).all()
+    assert (r["dist_out"] == 0).all()
+    assert (np.isinf(r["dist_in"]) & (r["dist_in"] > 0)).all()
+    assert (r["safety_in"] == 0).all() and (r["safety_out"] == 0).all()
+
+
+def test_tangent_to_concave_wall_enters():
+    """Full tube (5, 20, 30), points on r = 5, tangent directions d = (c t, w): the ray goes
+    into the wall at once and leaves through r = 20 after sqrt(20^2 - 5^2) / c."""
+    r, m = _gq("tube_inner_tangent", 3000, 32)
+    assert (r["inside"] == SURF).all()
+    assert (r["dist_in"] == 0).all()
+    want = math.sqrt(20.0 ** 2 - 5.0 ** 2) / m["c"]
+    assert np.abs(r["dist_out"] - want).max() <= 1e-9
+
+
+@pytest.mark.parametrize("fam", ["cone_outer_generator", "cone_inner_generator"])
+def test_ray_along_cone_generator(fam):
+    """Cone (0, 10, 5, 25, 40): points on the outer (inner) wall, directions along the
+    wall's straight generator up or down: the ray stays on the boundary to the end plane
+    and leaves there, so it never gets into the interior."""
+    r, m = _gq(fam, 3000, 33)
+    assert (r["inside"] == SURF).all()
+    assert (r["dist_out"] == 0).all()
+    assert (np.isinf(r["dist_in"]) & (r["dist_in"] > 0)).all()
+
+
+def test_ray_along_phi_plane():
+    """Tube (5, 20, 30, phi 0-270 deg), rays in the plane of the phi = 0 or phi = 270 deg face,
+    directions radial (+/-) with a small z part (xy length c):
+      on the face:          DistanceToOut 0; toward the axis the ray crosses the hole and
+                            enters at r = 5 on the opposite half-plane, (r0 + 5) / c away
+                            (phi + 180 deg is inside the segment), else no entry;
+      beyond rmax on it:    the same entry toward the axis, none away from it;
+      on the opposite half-plane (inside the solid): leaves at r = 5 or r = 20."""
+    r, m = _gq("phi_face_slide", 3000, 34)
+    k, r0, c, sg = m["kind"], m["r0"], m["c"], m["sign"]
+    toward = sg < 0
+    assert (r["inside"] == np.where(k == 0, SURF, np.where(k == 1, OUT, IN))).all()
+    on = k < 2
+    want_in = np.where(toward, (r0 + 5.0) / c, np.inf)
+    got = r["dist_in"][on]
+    fin = np.isfinite(want_in[on])
+    assert (np.isinf(got[~fin]) & (got[~fin] > 0)).all()
+    assert np.abs(got[fin] - want_in[on][fin]).max() <= 1e-9
+    assert (r["dist_out"][k == 0] == 0).all()
+    want_out = np.where(toward, (r0 - 5.0) / c, (20.0 - r0) / c)[k == 2]
+    assert np.abs(r["dist_out"][k == 2] - want_out).max() <= 1e-9
+
+
+def test_box_edge_touch_and_crossing():
+    """Box (10, 20, 30): rays through an edge point E at t0; a ray that arrives from
+    beyond one face and leaves beyond the adjacent one only touches (no entry), a ray
+    that arrives from beyond both faces enters at E."""
+    r, m = _gq("box_edge_touch", 3000, 35)
+    assert (r["inside"] == OUT).all()
+    touch = m["kind"] == 0
+    assert (np.isinf(r["dist_in"][touch]) & (r["dist_in"][touch] > 0)).all()
+    assert np.abs(r["dist_in"][~touch] - m["t0"][~touch]).max() <= 1e-9
+
+
+def test_box_face_slide():
+    """Box (10, 20, 30): rays in the plane of a face (the normal component exactly zero),
+    from the face (SURFACE: DistanceToOut 0, no entry) or from beyond its edge toward it
+    (the ray only runs along the face: no entry)."""
+    r, m = _gq("box_face_slide", 2000, 36)
+    on = m["kind"] == 0
+    assert (r["inside"][on] == SURF).all() and (r["inside"][~on] == OUT).all()
+    assert (r["dist_out"][on] == 0).all()
+    assert (np.isinf(r["dist_in"]) & (r["dist_in"] > 0)).all()
+
+
+def test_wall_touch_is_not_a_crossing():
+    """Full tube (5, 20, 30): a ray from inside the wall touching the hole r = 5 at t0 stays
+    in the solid and leaves through r = 20 at t0 + sqrt(20^2 - 5^2); a ray from outside
+    touching r = 20 never enters."""
+    r, m = _gq("hole_touch", 3000, 37)
+    assert (r["inside"] == IN).all()
+    want = m["t0"] + math.sqrt(20.0 ** 2 - 5.0 ** 2)
+    assert np.abs(r["dist_out"] - want).max() <= 1e-9
+    r, m = _gq("outer_touch", 3000, 38)
+    assert (r["inside"] == OUT).all()
+    assert (np.isinf(r["dist_in"]) & (r["dist_in"] > 0)).all()
+
+
+def test_end_plane_slide():
+    """Full tube (5, 20, 30): rays in the plane z = +/-30, from the end face (SURFACE:
+    DistanceToOut 0) or from beyond rmax toward the axis: they only run over the face."""
+    r, m = _gq("z_face_slide", 2000, 39)
+    out = m["out"]
+    assert (r["inside"][~out] == SURF).all() and (r["inside"][out] == OUT).all()
+    assert (r["dist_out"][~out] == 0).all()
+    assert (np.isinf(r["dist_in"]) & (r["dist_in"] > 0)).all()
+
+
 # ------------------------------------------------------------- golden
 
 def test_golden_analytic_cases():
@@ -658,6 +773,36 @@ def test_boolean_box_with_hole_closed_form():
     r2 = s.query(q[:, 0], q[:, 1], q[:, 2], one, zero, zero)
     assert (r2["inside"] == OUT).all()
     assert np.allclose(r2["dist_in"], 8.0 - 1e-3, atol=1e-9)                # re-enters at x = +4
+
+
+def test_boolean_slide_along_subtracted_face():
+    """Box (20, 20, 20) minus a box (5, 5, 30) through it along z.  On the hole's wall x = 5:
+    into the material (+x) the ray enters at once and leaves at x = 20 (15 mm); into the hole
+    (-x) it leaves at once and enters again at x = -5 (10 mm); along the wall (+/-z) it stays
+    on the boundary (no entry, DistanceToOut 0).  From above the box on the plane of that
+    wall the ray runs down the wall (no entry); beside the hole (|y| > 5) it enters at
+    z = 20."""
+    s = sol(_bool("subtraction", {"kind": "box", "params": (20.0, 20.0, 20.0)},
+                  {"kind": "box", "params": (5.0, 5.0, 30.0)}))
+    g = np.random.default_rng(40)
+    n = 400
+    y, z = g.uniform(-4, 4, n), g.uniform(-19, 19, n)
+    x = np.full(n, 5.0)
+    one, zero = np.ones(n), np.zeros(n)
+    r = s.query(x, y, z, one, zero, zero)
+    assert (r["inside"] == SURF).all() and (r["dist_in"] == 0).all()
+    assert np.abs(r["dist_out"] - 15.0).max() <= 1e-12
+    r = s.query(x, y, z, -one, zero, zero)
+    assert (r["dist_out"] == 0).all() and np.abs(r["dist_in"] - 10.0).max() <= 1e-12
+    for sz in (1.0, -1.0):
+        r = s.query(x, y, z, zero, zero, sz * one)
+        assert (r["dist_out"] == 0).all() and np.isinf(r["dist_in"]).all()
+    ztop = np.full(n, 25.0)
+    r = s.query(x, y, ztop, zero, zero, -one)
+    assert (r["inside"] == OUT).all() and np.isinf(r["dist_in"]).all()
+    yb = np.where(g.random(n) < 0.5, -1.0, 1.0) * g.uniform(6, 19, n)
+    r = s.query(x, yb, ztop, zero, zero, -one)
+    assert np.abs(r["dist_in"] - 5.0).max() <= 1e-12
 
 
 @pytest.mark.parametrize("idx", range(len(BOOL_SPECS)))

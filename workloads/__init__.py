@@ -531,3 +531,123 @@ def request_sizes(n_req: int, seed: int, lo: int = 1, hi: int = 65536) -> np.nda
 def poisson_arrivals(n_req: int, rate_per_s: float, seed: int) -> np.ndarray:
     g = rng(6000 + seed)
     return np.cumsum(g.exponential(1.0 / rate_per_s, n_req))
+
+
+# ------------------------------------------------------------ grazing rays
+#
+# Rays that touch a surface, run along it, or cross exactly through an edge: each
+# family places points on a surface (or on the plane or line of one) by construction
+# and gives directions that lie in it or touch it.  ``meta`` holds the construction
+# values (radii, touch distances, direction scale) that closed forms are written in.
+
+TUBE_FULL = {"kind": "tube", "params": (5.0, 20.0, 30.0, 0.0, TWO_PI)}
+
+GRAZING_FAMILIES = ("tube_outer_tangent", "tube_inner_tangent", "cone_outer_generator",
+                    "cone_inner_generator", "phi_face_slide", "box_edge_touch", "box_face_slide",
+                    "hole_touch", "outer_touch", "z_face_slide")
+
+
+def grazing_tracks(family: str, n: int, seed: int):
+    """(solid spec, tracks, meta) for one family of grazing rays."""
+    g = rng(seed)
+    one, zero = np.ones(n), np.zeros(n)
+    if family in ("tube_outer_tangent", "tube_inner_tangent"):
+        outer = family == "tube_outer_tangent"
+        spec = TUBE_M2 if outer else TUBE_FULL
+        R = 20.0 if outer else 5.0
+        ph = g.uniform(0.02, 1.5 * math.pi - 0.02 if outer else TWO_PI, n)
+        # a third exactly on the wall, the rest moved radially within the band
+        dr = np.where(np.arange(n) % 3 == 0, 0.0, g.uniform(-0.4e-9, 0.4e-9, n))
+        z = g.uniform(-20, 20, n)
+        w = np.where(g.random(n) < 0.5, 0.0, g.uniform(-0.3, 0.3, n))
+        c = np.sqrt(1 - w * w)
+        sg = np.where(g.random(n) < 0.5, -1.0, 1.0)
+        p = np.stack([(R + dr) * np.cos(ph), (R + dr) * np.sin(ph), z], 1)
+        d = np.stack([-sg * c * np.sin(ph), sg * c * np.cos(ph), w], 1)
+        return spec, soa(p, d), {"z": z, "w": w, "c": c}
+    if family in ("cone_outer_generator", "cone_inner_generator"):
+        spec = CONE_M2
+        a, r1 = (15.0 / 80.0, 10.0) if family == "cone_outer_generator" else (5.0 / 80.0, 0.0)
+        z = g.uniform(-39, 39, n)
+        R = a * (z + 40.0) + r1
+        ph = g.uniform(0, TWO_PI, n)
+        sg = np.where(g.random(n) < 0.5, -1.0, 1.0)
+        k = 1.0 / math.sqrt(1 + a * a)
+        p = np.stack([R * np.cos(ph), R * np.sin(ph), z], 1)
+        d = sg[:, None] * np.stack([a * k * np.cos(ph), a * k * np.sin(ph), k * one], 1)
+        return spec, soa(p, d), {"z": z, "sign": sg}
+    if family == "phi_face_slide":
+        spec = TUBE_M2
+        face = np.where(g.random(n) < 0.5, 0.0, 1.5 * math.pi)
+        kind = g.integers(0, 3, n)  # 0: on the face, 1: beyond rmax on its plane, 2: the interior half-plane
+        r0 = np.where(kind == 0, g.uniform(6, 19, n), np.where(kind == 1, g.uniform(21, 30, n), g.uniform(6, 19, n)))
+        phr = np.where(kind == 2, face + math.pi, face)
+        z = g.uniform(-10, 10, n)
+        w = np.where(g.random(n) < 0.5, 0.0, g.uniform(-0.3, 0.3, n))
+        c = np.sqrt(1 - w * w)
+        sg = np.where(g.random(n) < 0.5, -1.0, 1.0)  # +1 away from the axis
+        p = np.stack([r0 * np.cos(phr), r0 * np.sin(phr), z], 1)
+        d = np.stack([sg * c * np.cos(phr), sg * c * np.sin(phr), w], 1)
+        return spec, soa(p, d), {"kind": kind, "r0": r0, "c": c, "sign": sg}
+    if family in ("box_edge_touch", "box_face_slide"):
+        spec = BOX_M1
+        D = np.array(spec["params"])
+        p = np.empty((n, 3))
+        d = np.zeros((n, 3))
+        meta = {"t0": np.zeros(n), "kind": np.zeros(n, int)}
+        for m in range(n):
+            i, j = g.choice(3, 2, replace=False)
+            k = 3 - i - j
+            si, sj = g.choice([-1.0, 1.0], 2)
+            if family == "box_edge_touch":
+                E = np.zeros(3)
+                E[i], E[j], E[k] = si * D[i], sj * D[j], g.uniform(-D[k] + 1, D[k] - 1)
+                beta = g.uniform(0.1, 1.4)
+                through = g.random() < 0.25  # a quarter cross the edge into the box
+                e = np.zeros(3)
+                e[i] = -si * math.cos(beta)
+                e[j] = (-sj if through else sj) * math.sin(beta)
+                e[k] = g.uniform(-0.3, 0.3) if g.random() < 0.5 else 0.0
+                e /= np.linalg.norm(e)
+                t0 = g.uniform(1, 10)
+                p[m] = E - t0 * e
+                d[m] = e
+                meta["t0"][m], meta["kind"][m] = t0, int(through)
+            else:
+                q = g.uniform(-1, 1, 3) * (D - 1)
+                q[i] = si * D[i]
+                out = g.random() < 0.5  # beyond the face's edge, on its plane
+                if out:
+                    q[j] = sj * (D[j] + g.uniform(1, 10))
+                e = np.zeros(3)
+                ang = g.uniform(0, TWO_PI)
+                e[j], e[k] = math.cos(ang), math.sin(ang)
+                if out:
+                    e[j] = -sj * abs(e[j])  # toward the face
+                p[m], d[m] = q, e
+                meta["kind"][m] = int(out)
+        return spec, soa(p, d), meta
+    if family in ("hole_touch", "outer_touch"):
+        spec = TUBE_FULL
+        R = 5.0 if family == "hole_touch" else 20.0
+        ph = g.uniform(0, TWO_PI, n)
+        z = g.uniform(-20, 20, n)
+        t0 = g.uniform(1, 15, n)
+        T = np.stack([R * np.cos(ph), R * np.sin(ph), z], 1)
+        e = np.stack([-np.sin(ph), np.cos(ph), zero], 1)
+        return spec, soa(T - t0[:, None] * e, e), {"t0": t0}
+    if family == "z_face_slide":
+        spec = TUBE_FULL
+        top = np.where(g.random(n) < 0.5, 30.0, -30.0)
+        out = g.random(n) < 0.4
+        rr = np.where(out, g.uniform(21, 40, n), g.uniform(6, 19, n))
+        ph = g.uniform(0, TWO_PI, n)
+        ang = g.uniform(0, TWO_PI, n)
+        dxy = np.stack([np.cos(ang), np.sin(ang)], 1)
+        # points beyond rmax move toward the axis
+        toward = -np.stack([np.cos(ph), np.sin(ph)], 1)
+        dxy = np.where(out[:, None], toward, dxy)
+        p = np.stack([rr * np.cos(ph), rr * np.sin(ph), top], 1)
+        d = np.stack([dxy[:, 0], dxy[:, 1], zero], 1)
+        return spec, soa(p, d), {"out": out}
+    raise ValueError(family)
