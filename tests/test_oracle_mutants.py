@@ -44,6 +44,10 @@ MUTANTS = {
     "boolean placement ignored": ("const double v[3] = {p[0] - b->t[0], p[1] - b->t[1], p[2] - b->t[2]};",
                                   "const double v[3] = {p[0], p[1], p[2]};"),
     "boolean union safety max": ("if (to_in) return dmin(sia, sic);", "if (to_in) return dmax(sia, sic);"),
+    "trap axis azimuth swapped": ("const double cx = zf * tthc, cy = zf * tths;", "const double cx = zf * tths, cy = zf * tthc;"),
+    "trap face quad from the wrong vertices": ("if (face_plane(v[0], v[4], v[6], v[2], cs, &s->pl[4])) return -1;",
+                                               "if (face_plane(v[0], v[4], v[7], v[3], cs, &s->pl[4])) return -1;"),
+    "section line offset taken at the far plane": ("L->b = r0 - L->a * z0;", "L->b = r0 - L->a * z1;"),
     "tangent threshold dropped": ("#define OR_TAU 1e-12", "#define OR_TAU 0.0"),
     "tangent convex wall entered": ("return outer ? 1 : -1;", "return outer ? -1 : 1;"),
     "generator ray taken as curved": ("if (r > 0 && fabs(p[0] * d[1] - p[1] * d[0]) > OR_TAU * r)", "if (r > 0)"),

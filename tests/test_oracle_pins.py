@@ -56,6 +56,54 @@ def test_box_membership_by_construction():
     assert (b.inside(deep_in) == IN).all() and (b.inside(far_out) == OUT).all()
 
 
+def _trap_faces(params):
+    """The six faces of a trap from its vertices (workloads._trap_vertices, plain numpy):
+    per face its centroid and outward unit normal, the normal fitted by a singular value
+    decomposition of the face's four vertices (not the library's diagonal cross product)."""
+    V = W._trap_vertices(params)
+    centre = V.mean(axis=0)
+    quads = [(0, 1, 2, 3), (4, 5, 6, 7), (0, 1, 5, 4), (2, 3, 7, 6), (0, 2, 6, 4), (1, 3, 7, 5)]
+    out = []
+    for q in quads:
+        P = V[list(q)]
+        c = P.mean(axis=0)
+        _, sv, vt = np.linalg.svd(P - c)
+        assert sv[-1] < 1e-9 * max(1.0, sv[0])  # planar
+        n = vt[-1]
+        if np.dot(n, c - centre) < 0:
+            n = -n
+        out.append((c, n))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_trap_membership_by_construction(seed):
+    """Random traps (tilted axis, sheared faces, unequal half-lengths): points at each face's
+    centroid moved along the face's own normal by -0.7e-9 (INSIDE), +/-0.4e-9 (SURFACE) and
+    +0.7e-9 mm (OUTSIDE); the face centroid moved 1 mm inward is INSIDE with SafetyToOut 1 for
+    a face nearer than every other."""
+    g = np.random.default_rng(70 + seed)
+    for j in range(8):
+        spec = W.trap_random(g)
+        if j % 2:  # the axis at any azimuth, tilted up to 30 deg
+            p = list(spec["params"][0])
+            p[1], p[2] = g.uniform(0, 30) * W.DEG, g.uniform(0, 360) * W.DEG
+            spec = {"kind": "trap", "params": (tuple(p),)}
+        params = spec["params"][0]
+        s = sol(spec)
+        faces = _trap_faces(params)
+        for c, n in faces:
+            pts = np.array([c - 0.7e-9 * n, c - 0.4e-9 * n, c + 0.4e-9 * n, c + 0.7e-9 * n])
+            assert list(s.inside(pts)) == [IN, SURF, SURF, OUT], (params, c, n)
+        # unit step inward from the face with the largest inscribed distance at its centroid
+        for c, n in faces:
+            q = c - 1.0 * n
+            others = [np.dot(q - c2, n2) for c2, n2 in faces]
+            if max(others) < -1.0 + 1e-9 and sorted(others)[-2] < -1.0 - 1e-6:
+                r = s.query([q[0]], [q[1]], [q[2]], [0.0], [0.0], [1.0], want=("inside", "safety_out"))
+                assert r["inside"][0] == IN and r["safety_out"][0] == pytest.approx(1.0, abs=1e-9)
+
+
 def _slab(D, p, d):
     """Textbook slab method for an axis-aligned box (Kay-Kajiya), per track."""
     tn, tf = -np.inf, np.inf
