@@ -24,6 +24,12 @@ enum BoolOp : int32_t { kUnion = 0, kSubtraction = 1, kIntersection = 2 };
 
 constexpr int kMaxZ = 32;            // polycone z-planes (GV_MAX_ZPLANES)
 constexpr double kHalfTol = 0.5e-9;  // h = kTolerance / 2 (mm)
+// Grazing rays: a derivative per unit length within kTangent of zero is tangent; crossings
+// closer than kMerge (mm) are one crossing; a quadratic's discriminant within kDisc times its
+// rounding scale is a double root (a touch).
+constexpr double kTangent = 1e-12;
+constexpr double kMerge = 1e-12;
+constexpr double kDisc = 16 * 1.1102230246251565e-16;
 
 enum : int32_t { kHasPhi = 1, kPhiWide = 2 };
 

@@ -17,7 +17,11 @@
 // bound is below half the stated tolerance (1e-5 relative; 1e-9 mm below 1e-4 mm).
 // Near ties (a ray grazing an edge, a tangent root, an entry point on another
 // surface) are flagged, as are the surface-start cases of the polycone family
-// that need the full set of rules.  No binary64 instruction is used here.
+// that need the full set of rules.  So is every track that the binary64 rules for
+// grazing rays could decide: a constraint within reach of the band whose derivative
+// along d is within reach of the tangent threshold (a ray along or tangent to a
+// surface), and two crossings within reach of the merge distance.  No binary64
+// instruction is used here.
 #pragma once
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -31,6 +35,8 @@ constexpr float U = 5.9604645e-8f;      // 2^-24
 constexpr float G42 = 2.2737368e-13f;   // 2^-42
 constexpr float HF = 5e-10f;            // h
 constexpr float FLOOR = 1e-15f;         // absolute floor of every decision bound
+constexpr float TAUF = 2.5e-12f;        // > kTangent: derivatives per unit length this small are flagged
+constexpr float MERGEF = 2.5e-12f;      // > kMerge: crossings this close are not told apart
 #define F_INF CUDART_INF_F
 
 enum : unsigned { kWantCode = 1, kWantDin = 2, kWantDout = 4, kWantSin = 8, kWantSout = 16 };
@@ -78,8 +84,8 @@ __device__ __forceinline__ bool certified(Val t) {
   const float tol = t.v < 1e-4f ? 1e-9f : 1e-5f * t.v;
   return t.e <= 0.5f * tol;
 }
-// a < b decided with certainty?
-__device__ __forceinline__ bool apart(Val a, Val b) { return fabsf(a.v - b.v) > a.e + b.e; }
+// a < b decided with certainty (and farther apart than the merge distance)?
+__device__ __forceinline__ bool apart(Val a, Val b) { return fabsf(a.v - b.v) > (a.e + b.e) + MERGEF; }
 
 // ------------------------------------------------------------ conversions
 
@@ -254,15 +260,17 @@ __device__ inline void box32(const Desc& S, const TrackF& T, unsigned want, R32&
       any_out |= gd > 0;
       all_in &= gd < 0;
     }
+    // along or nearly along the face plane: sliding is decided in binary64
+    if (fabsf(d[i]) <= TAUF + (FRAME ? 4.f * T.dfl : 0.f) && fabsf(g[i].g) <= HF + g[i].E) R.flag = true;
     if (R.code == 1 && fabsf(g[i].g + HF) <= g[i].E) R.flag = true;
   }
   if (want & kWantDout) {
     if (R.code == 2) R.dout = -1.f;
-    else if (R.code == 1 && any_out) R.dout = 0.f;
+    else if (R.code == 1 && !all_in) R.dout = 0.f;
     else {
       if (!certified(tf)) R.flag = true;
       R.dout = unbig(tf.v);
-      if (R.code == 1) {  // a surface point not leaving: inside (no tolerance) halfway to the exit?
+      if (R.code == 1) {  // an entering surface point: inside (no tolerance) halfway to the exit?
         const float h = 0.5f * tf.v;
         float sm = -BIG, em = 0.f;
         for (int i = 0; i < 3; i++) {
@@ -319,6 +327,8 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
   Val tn{-BIG, 0.f}, tf{BIG, 0.f};
   bool miss = false, any_out = false, all_in = true;
   for (int i = 0; i < 4; i++) {
+    // along or nearly along the face plane: sliding is decided in binary64
+    if (fabsf(gd[i]) <= egd[i] + TAUF && fabsf(g[i].g) <= HF + g[i].E) R.flag = true;
     if (fabsf(gd[i]) <= egd[i]) {  // nearly parallel: which side it stays on must be certain
       if (fabsf(g[i].g) <= g[i].E || R.code == 1) R.flag = true;
       miss |= g[i].g > 0;
@@ -333,6 +343,7 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
   }
   {  // z slab
     const bool toward = (T.zh < 0) == (T.w < 0);
+    if (fabsf(T.w) <= egd[4] + TAUF && fabsf(g[4].g) <= HF + g[4].E) R.flag = true;
     if (FRAME && fabsf(T.w) <= 4.f * T.dfl) R.flag = true;  // sign of w not certain
     if (T.w == 0) {
       if (fabsf(g[4].g) <= g[4].E) R.flag = true;
@@ -353,17 +364,17 @@ __device__ inline void planar32(const Desc& S, const TrackF& T, unsigned want, R
     if (g[i].g >= -HF) {
       any_out |= gd[i] > 0;
       all_in &= gd[i] < 0;
-      if (R.code == 1 && i < 4 && fabsf(gd[i]) <= egd[i]) R.flag = true;
+      if (R.code == 1 && fabsf(gd[i]) <= egd[i] + TAUF) R.flag = true;
     }
     if (R.code == 1 && fabsf(g[i].g + HF) <= g[i].E) R.flag = true;
   }
   if (want & kWantDout) {
     if (R.code == 2) R.dout = -1.f;
-    else if (R.code == 1 && any_out) R.dout = 0.f;
+    else if (R.code == 1 && !all_in) R.dout = 0.f;
     else {
       if (!certified(tf)) R.flag = true;
       R.dout = unbig(tf.v);
-      if (R.code == 1) {  // a surface point not leaving: inside (no tolerance) halfway to the exit?
+      if (R.code == 1) {  // an entering surface point: inside (no tolerance) halfway to the exit?
         const float h = 0.5f * tf.v;
         const float qx = fmaf(h, T.u, T.xh), qy = fmaf(h, T.v, T.yh), qz = fmaf(h, T.w, T.zh);
         float sm = fabsf(qz) - S.dzh, em = 4.f * U * (fabsf(qz) + S.dzh);
@@ -567,6 +578,7 @@ __device__ __forceinline__ Iv iv_region(const Quad& q, float g, float Eg, bool& 
 }
 // Half-space {n.p <= 0} (want_le) or {n.p > 0} crossed at t = -a / nd.
 __device__ __forceinline__ Iv iv_half(float a, float Ea, float nd, float end, bool want_le, bool& unsure) {
+  if (fabsf(nd) <= end + TAUF && fabsf(a) <= HF + Ea) unsure = true;  // along the plane: binary64
   if (fabsf(nd) <= end) {
     if (fabsf(a) <= Ea) unsure = true;
     return ((a <= 0) == want_le) ? iv_all() : iv_none();
@@ -774,6 +786,28 @@ __device__ inline bool pcon_begin(const Desc& S, const TrackF& T, unsigned want,
     ends = 6.f * U * (fabsf(S.nsh[0] * T.u) + fabsf(S.nsh[1] * T.v)) + (FRAME ? 1.5f * T.dfl : 0.f) + 1e-30f;
     ende = 6.f * U * (fabsf(S.neh[0] * T.u) + fabsf(S.neh[1] * T.v)) + (FRAME ? 1.5f * T.dfl : 0.f) + 1e-30f;
   }
+  // Derivatives along d and their bounds, widened by the tangent threshold (the lateral
+  // ones are r times the derivative per unit length over k).
+  const float ao = TUBE ? 0.f : S.oah[k0], ai = TUBE ? 0.f : S.iah[k0];
+  const float ew = FRAME ? T.dfl : 0.f;
+  const float gdo = radial - ao * T.w * rh, gdi = -(radial - ai * T.w * rh);
+  const float egdo = eRadial + 4.f * U * fabsf(ao * T.w * rh) + fabsf(ao) * rh * ew + 2.f * TAUF * rh * (1.f + fabsf(ao));
+  const float egdi = eRadial + 4.f * U * fabsf(ai * T.w * rh) + fabsf(ai) * rh * ew + 2.f * TAUF * rh * (1.f + fabsf(ai));
+  const float ewz = ew + TAUF, endsT = ends + TAUF, endeT = ende + TAUF;
+  // A constraint within reach of the band that the ray may run along (any start): binary64.
+  {
+    auto slide_chk = [&](float g, float Eg, float gd, float egd) {
+      if (fabsf(g) <= HF + Eg && fabsf(gd) <= egd) R.flag = true;
+    };
+    slide_chk(lo_.g, lo_.E, gdo, egdo);
+    if (has_in) slide_chk(li_.g, li_.E, gdi, egdi);
+    slide_chk(gz0, Ez0, -T.w, ewz);
+    slide_chk(gz1, Ez1, T.w, ewz);
+    if (has_phi) {
+      slide_chk(pa.g, pa.E, nds, endsT);
+      slide_chk(pb.g, pb.E, nde, endeT);
+    }
+  }
   // surface start: decided here only when some constraint certainly grows (leaving)
   // or every one certainly shrinks (entering); the other surface cases go to binary64.
   bool any_out = false, all_in = true, unsure = false;
@@ -786,19 +820,17 @@ __device__ inline bool pcon_begin(const Desc& S, const TrackF& T, unsigned want,
         if (!(gd < 0)) all_in = false;
       }
     };
-    const float ao = TUBE ? 0.f : S.oah[k0], ai = TUBE ? 0.f : S.iah[k0];
-    const float ew = FRAME ? T.dfl : 0.f;
-    add(lo_.g, lo_.E, radial - ao * T.w * rh, eRadial + 4.f * U * fabsf(ao * T.w * rh) + fabsf(ao) * rh * ew);
-    if (has_in) add(li_.g, li_.E, -(radial - ai * T.w * rh), eRadial + 4.f * U * fabsf(ai * T.w * rh) + fabsf(ai) * rh * ew);
-    add(gz0, Ez0, -T.w, ew);
-    add(gz1, Ez1, T.w, ew);
+    add(lo_.g, lo_.E, gdo, egdo);
+    if (has_in) add(li_.g, li_.E, gdi, egdi);
+    add(gz0, Ez0, -T.w, ewz);
+    add(gz1, Ez1, T.w, ewz);
     if (has_phi) {
       if (wide) {
         if (fabsf(pa.g - pb.g) <= pa.E + pb.E) unsure = true;
-        if (pa.g <= pb.g) add(pa.g, pa.E, nds, ends); else add(pb.g, pb.E, nde, ende);
+        if (pa.g <= pb.g) add(pa.g, pa.E, nds, endsT); else add(pb.g, pb.E, nde, endeT);
       } else {
-        add(pa.g, pa.E, nds, ends);
-        add(pb.g, pb.E, nde, ende);
+        add(pa.g, pa.E, nds, endsT);
+        add(pb.g, pb.E, nde, endeT);
       }
     }
   }

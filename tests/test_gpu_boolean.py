@@ -42,6 +42,42 @@ def test_boolean_parity(gv, i):
     assert ws.refined() == 0
 
 
+def test_boolean_grazing(gv):
+    """A box with a square through-hole (subtraction): points on the hole's wall and on its
+    plane above the box, rays into the material, into the hole and along the wall, plus
+    rays touching the outer box's edges: parity with the oracle at 1e-9 mm."""
+    import torch
+    spec = {"kind": "boolean", "params": ("subtraction", {"kind": "box", "params": (20.0, 20.0, 20.0)},
+                                          {"kind": "box", "params": (5.0, 5.0, 30.0)}, np.eye(3), np.zeros(3))}
+    g = np.random.default_rng(41)
+    n = 3000
+    y, z = g.uniform(-4, 4, n), g.uniform(-19, 19, n)
+    p = np.stack([np.full(n, 5.0), y, z], 1)
+    k = g.integers(0, 5, n)
+    d = np.zeros((n, 3))
+    d[k == 0, 0], d[k == 1, 0], d[k == 2, 2], d[k == 3, 2] = 1.0, -1.0, 1.0, -1.0
+    a = g.uniform(0, 2 * np.pi, n)
+    d[k == 4, 1], d[k == 4, 2] = np.cos(a[k == 4]), np.sin(a[k == 4])  # in the wall's plane
+    top = g.random(n) < 0.3
+    p[top, 2] = 25.0
+    d[top] = [0.0, 0.0, -1.0]
+    tr = W.soa(p, d)
+    s = gv.Solid.from_spec(spec)
+    got = gv.query(s, to_device(tr, torch), precision="fp64")
+    torch.cuda.synchronize()
+    compare(to_host(got), oracle.Solid.from_spec(spec).query(**tr), "fp64", "hole-wall")
+    # the outer box's edges, touched and crossed: the box family for (10, 20, 30) mapped onto
+    # (20, 20, 20) by an axis scaling (lines touching an edge stay lines touching the edge)
+    _, tb, _ = W.grazing_tracks("box_edge_touch", 2000, 42)
+    sc = np.array([2.0, 1.0, 2.0 / 3.0])
+    P = np.stack([tb["x"], tb["y"], tb["z"]], 1) * sc
+    D = np.stack([tb["dx"], tb["dy"], tb["dz"]], 1) * sc
+    tb = W.soa(P, D / np.linalg.norm(D, axis=1, keepdims=True))
+    got = gv.query(s, to_device(tb, torch), precision="fp64")
+    torch.cuda.synchronize()
+    compare(to_host(got), oracle.Solid.from_spec(spec).query(**tb), "fp64", "outer-edges")
+
+
 def test_boolean_in_batch_and_navigation(gv):
     import torch
     # a batch mixing booleans and primitives
