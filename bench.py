@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, navigation and serving forms")
-    ap.add_argument("--form", default="all", choices=["all", "batched", "transport"],
+    ap.add_argument("--form", default="all", choices=["all", "batched", "transport", "peaks"],
                     help="batched / transport: only that form (for profiling), --warmup then --steps calls")
     return ap.parse_args()
 
@@ -144,6 +144,43 @@ def cpu_baseline(tracks_per_solid: dict, sample: int):
             "sample": f"first {sample} tracks of each of the 5 solids' 2^24-track baskets, all five queries"}
 
 
+def cpu_closed_form(tracks_per_solid: dict, oracle_sample: int, sample: int = 1 << 20):
+    """The fair CPU baseline (cpu_baseline/: the binary64 closed forms compiled for the host),
+    on all host cores over the first `sample` tracks of each solid and on one core over a
+    sixteenth of that, all five queries; checked against the oracle on the oracle's sample."""
+    import cpu_baseline
+    import oracle
+    threads = os.cpu_count() or 1
+    res = {"kind": "closed-form binary64 loop (the library's binary64 solid code on the host)",
+           "cores": threads, "unit": "queries/s"}
+    for label, th, m in (("allcores", threads, sample), ("1core", 1, sample // 16)):
+        total, t = 0, 0.0
+        for name, spec in specs():
+            tr = {k: v[:m] for k, v in tracks_per_solid[name].items()}
+            c = cpu_baseline.Solid(spec)
+            t0 = time.perf_counter()
+            c.query(**tr, threads=th)
+            t += time.perf_counter() - t0
+            total += m
+        res[f"{label}_value"] = total * N_QUERIES / t
+        res[f"{label}_sample"] = f"first {m} tracks of each of the 5 solids' baskets"
+    # parity with the oracle on its sample: codes equal; zeros, -1 and +inf equal; others within 1e-9 mm
+    bad = 0
+    for name, spec in specs():
+        tr = {k: v[:oracle_sample] for k, v in tracks_per_solid[name].items()}
+        got = cpu_baseline.Solid(spec).query(**tr, threads=threads)
+        want = oracle.Solid.from_spec(spec).query(**tr, threads=threads)
+        bad += int((got["inside"] != want["inside"]).sum())
+        for k in ("dist_in", "dist_out", "safety_in", "safety_out"):
+            g, w = got[k], want[k]
+            special = ~np.isfinite(w) | (w <= 0)
+            with np.errstate(invalid="ignore"):
+                ok = np.where(special, (g == w) | (np.isinf(g) & np.isinf(w)), np.abs(g - w) <= 1e-9)
+            bad += int((~ok).sum())
+    res["parity_vs_oracle"] = {"mismatches": bad, "tracks": 5 * oracle_sample, "tolerance_mm": 1e-9}
+    return res
+
+
 def cpu_baseline_extras():
     """The oracle beside the other forms, all host cores, on bounded samples of their
     workloads: the transport loop (nested detector, 16384 tracks, kmax 64), boolean solids
@@ -183,13 +220,15 @@ def cpu_baseline_extras():
 
 
 def cpu_baseline_sweep(max_exp: int = 16):
-    """The oracle on the sweep's tracks for N <= 2^max_exp, one core and all cores
-    (DistanceToOut only), for the GPU-over-CPU ratio of the paper's figure."""
+    """The oracle and the closed-form CPU loop on the sweep's tracks for N <= 2^max_exp, one
+    core and all cores (DistanceToOut only), for the GPU-over-CPU ratio of the paper's figure."""
+    import cpu_baseline
     import oracle
     threads = os.cpu_count() or 1
     res = {}
     for name, spec in SWEEP_SPECS:
         o = oracle.Solid.from_spec(spec)
+        c = cpu_baseline.Solid(spec)
         rows = []
         for e in SWEEP_EXPONENTS:
             if e > max_exp:
@@ -203,6 +242,11 @@ def cpu_baseline_sweep(max_exp: int = 16):
                 for _ in range(reps):
                     o.query(**tr, threads=th, want=("dist_out",))
                 row[f"oracle_{label}_tracks_per_s"] = n * reps / (time.perf_counter() - t0)
+                reps = max(1, min(2000, (1 << 18) // n))
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    c.query(**tr, threads=th, want=("dist_out",))
+                row[f"closed_form_{label}_tracks_per_s"] = n * reps / (time.perf_counter() - t0)
             rows.append(row)
         res[name] = rows
     return {"cores": threads, "rows": res}
@@ -373,6 +417,7 @@ def run_ours(args):
             line["serving"] = bench_serving(gv, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(inputs, args.cpu_sample)
+        line["cpu_closed_form"] = cpu_closed_form(inputs, args.cpu_sample)
         if not args.no_extra:
             line["sweep_dist_out_oracle"] = cpu_baseline_sweep()
             line["oracle_extras"] = cpu_baseline_extras()
@@ -677,7 +722,7 @@ def bench_voxels(gv, torch, reps=3, n=1 << 20, n_transport=1 << 18, kmax=32):
 def bench_serving(gv, torch, seconds=1.5):
     """Continuous batching: Poisson arrivals of navigation requests with sizes
     log-uniform in 1-65536 tracks; saturated throughput first, then p50/p99 latency at
-    50% and 80% of it."""
+    50%, 80% and 95% of it."""
     import time as _t
     geo = W.nested_geometry()
     G = gv.Geometry(geo["solids"], geo["nodes"])
@@ -708,7 +753,7 @@ def bench_serving(gv, torch, seconds=1.5):
            "saturated_requests_per_s": sat_rate,
            "saturated_tracks_per_s": sum(n for _, n in tickets) / (_t.perf_counter() - t0)}
     g = np.random.default_rng(11)
-    for rho in (0.5, 0.8):
+    for rho in (0.5, 0.8, 0.95):
         srv.reset_stats()
         rate = rho * sat_rate
         t_next = _t.perf_counter()
@@ -745,6 +790,51 @@ def load_peaks():
         return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json, copy)"}
     except (OSError, KeyError, ValueError):
         return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def bench_alu_peaks(torch, index: int, reps: int = 5):
+    """Measured ALU-side peaks (probe/gvprobe.cu): binary32 and binary64 multiply-adds, an
+    integer-pipe step (a funnel shift and an xor), and the warp-instruction issue rate (binary32
+    multiply-adds and integer steps on separate chains), each as the best of `reps` CUDA-event
+    timed launches of 8 blocks of 256 threads per SM, with the SM clock sampled meanwhile.
+    Rates per clock and SM use the sampled median clock."""
+    import ctypes
+    from paper_1512_06637_gb300 import build
+    lib = ctypes.CDLL(build.build_probe())
+    props = torch.cuda.get_device_properties(index)
+    sms = props.multi_processor_count
+    threads, blocks = 256, sms * 8
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # (name, function, iterations, operations per thread per iteration, warp instructions per op)
+    probes = [("fp32_fma", lib.gvp_fma32, 4096, 16 * 8), ("fp64_fma", lib.gvp_fma64, 128, 16 * 8),
+              ("alu_step", lib.gvp_alu, 2048, 16 * 8), ("issue_mix", lib.gvp_issue, 4096, 16 * 8)]
+    clocks = ClockSampler(index)
+    clocks.start()
+    time.sleep(0.3)
+    best = {}
+    for name, fn, iters, per_iter in probes:
+        ms = ctypes.c_float(0.0)
+        times = []
+        for _ in range(reps + 1):
+            rc = fn(blocks, threads, iters, ctypes.c_void_p(sink.data_ptr()), stream, ctypes.byref(ms))
+            if rc != 0:
+                raise RuntimeError(f"probe {name} failed")
+            times.append(ms.value)
+        best[name] = (min(times[1:]), iters * per_iter * threads * blocks)
+    ck = clocks.stop()
+    mhz = ck["sm_mhz"] or ck["sm_max_mhz"] or 2070.0
+    out = {"sms": sms, "sm_mhz": mhz, "clocks": ck}
+    for name, (ms, ops) in best.items():
+        per_s = ops / (ms * 1e-3)
+        out[name] = {"ms": ms, "ops_per_s": per_s, "per_clk_per_sm": per_s / (sms * mhz * 1e6)}
+    # warp instructions per clock per SM: a binary32 multiply-add is one instruction per thread,
+    # so the multiply-add probe's rate / 32 is the issue rate it reached (the mixed probe shows
+    # whether two pipes together get past it)
+    out["issue_warp_inst_per_clk_per_sm"] = out["fp32_fma"]["per_clk_per_sm"] / 32.0
+    out["fp32_flops"] = 2 * out["fp32_fma"]["ops_per_s"]
+    out["fp64_flops"] = 2 * out["fp64_fma"]["ops_per_s"]
+    return out
 
 
 def run_batched_only(args):
@@ -796,6 +886,12 @@ def main():
         run_batched_only(args)
     elif args.form == "transport":
         run_transport_only(args)
+    elif args.form == "peaks":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_1512_06637_gb300 import build
+        build.build()
+        print(json.dumps({"form": "peaks", **bench_alu_peaks(torch, torch.cuda.current_device())}), flush=True)
     else:
         run_ours(args)
 

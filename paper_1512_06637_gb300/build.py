@@ -19,6 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgvgeo.so")
+PROBE = os.path.join(PKG, "libgvprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -79,7 +80,23 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
+    build_probe(force)
     return LIB
+
+
+def build_probe(force: bool = False) -> str:
+    """The benchmark's throughput probes (``probe/gvprobe.cu`` -> ``libgvprobe.so``): binary32
+    and binary64 multiply-add, integer-pipe and instruction-issue rates.  Not part of the
+    geometry library."""
+    src = os.path.join(PKG, "probe", "gvprobe.cu")
+    if force or _stale(PROBE, [src, os.path.abspath(__file__)]):
+        tmp = PROBE + f".tmp{os.getpid()}"
+        cmd = [nvcc(), src, "-shared", "-o", tmp, "-lcudart"] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PROBE)
+    return PROBE
 
 
 if __name__ == "__main__":

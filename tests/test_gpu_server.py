@@ -1,7 +1,8 @@
 """The continuous-batching navigation service (C ABI, worker thread, device arena).
 
 Every request's results are bit-identical to the same tracks computed alone
-(locate + step through the direct calls) and agree with the oracle; requests
+(locate + step through the direct calls) and agree with the oracle (node and next
+exactly, step and safety at the stated tolerances, zeros and sentinels exactly); requests
 arrive while others are on the GPU; a request that can never fit is refused; a
 wait on a request that cannot be admitted yet times out with a status and the
 service stays usable.
@@ -72,9 +73,14 @@ def test_server_alone_equals_mix(gv, geo, precision):
         assert np.array_equal(onode, got["node"])
         w = O.nav_step(tr["x"], tr["y"], tr["z"], tr["dx"], tr["dy"], tr["dz"], onode)
         assert np.array_equal(w["next"], got["next"])
-        fin = np.isfinite(w["step"]) & (w["step"] > 0)
-        tol = 1e-9 if precision == "fp64" else np.maximum(1e-9, 1e-5 * np.abs(w["step"][fin]))
-        assert (np.abs(got["step"][fin] - w["step"][fin]) <= tol).all()
+        for k in ("step", "safety"):
+            want = w[k]
+            assert np.array_equal(np.isfinite(want), np.isfinite(got[k])), k
+            assert np.array_equal(want <= 0, got[k] <= 0), k
+            assert np.array_equal(got[k][want <= 0], want[want <= 0]), k  # zeros and sentinels exactly
+            fin = np.isfinite(want) & (want > 0)
+            tol = 1e-9 if precision == "fp64" else np.maximum(1e-9, 1e-5 * np.abs(want[fin]))
+            assert (np.abs(got[k][fin] - want[fin]) <= tol).all(), k
     srv.close()
 
 
