@@ -369,9 +369,12 @@ void gv_server_destroy(gv_server* s);
  * All calls share the one array: the counter is cleared on `stream` at the start
  * of each call and the worklist keeps the last call's contents, so calls that
  * overlap on the GPU race and must be serialised by the caller.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress); make
- * it before any stream capture.  Results, arguments and errors otherwise as for
- * gv_query with GV_FP32_REFINE. */
+ * on a device with a non-empty basket looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it; make that call before any stream capture.
+ * The kept address belongs to the device's primary context: it does not survive
+ * cudaDeviceReset, and callers in another (driver-API) context must not use this
+ * entry point.  An empty basket returns GV_OK and enqueues nothing.  Results,
+ * arguments and errors otherwise as for gv_query with GV_FP32_REFINE. */
 gv_status gv_query_fp32_static(const gv_solid* s, const gv_tracks* tracks, const gv_results* res,
                                void* stream);
 

@@ -20,10 +20,13 @@
 //    whatever the last call left in it.  Calls that overlap on the GPU (on
 //    different streams, or from different threads) race on the array and give
 //    wrong results: serialise them;
-//  - the first call on a device resolves the array's device address with
-//    cudaGetSymbolAddress (host code cannot use the symbol itself: in host code
-//    its name stands for a host-side shadow, not a device address).  Make that
-//    first call before any stream capture.
+//  - the first call on a device with a non-empty basket resolves the array's
+//    device address with cudaGetSymbolAddress (host code cannot use the symbol
+//    itself: in host code its name stands for a host-side shadow, not a device
+//    address) and keeps it for that device.  Make that first call before any
+//    stream capture.  The kept address belongs to the device's primary context as
+//    it was when first resolved: it does not survive cudaDeviceReset, and a caller
+//    running in another (driver-API) context must not use this entry point.
 #include <mutex>
 #include "gv_internal.h"
 
@@ -79,6 +82,7 @@ extern "C" gv_status gv_query_fp32_static(const gv_solid* s, const gv_tracks* t,
       if (ptrs[i] && ((uintptr_t)ptrs[i] & 7u))
         return set_error(GV_ERR_INVALID_ARG, "gv_query_fp32_static: arrays must be 8-byte aligned");
   }
+  if (t->n == 0) return GV_OK;  // nothing to do: nothing enqueued, no address looked up
   void* base = nullptr;
   gv_status st = static_scratch(&base);
   if (st != GV_OK) return st;
