@@ -1,8 +1,9 @@
 // query_fp32.cu -- the binary32 bulk pass with binary64 refinement.
 //
 // Pass 1 (k_query_fp32): one thread per track; the solid descriptor staged in
-// shared memory; inputs read as raw 64-bit words and split into binary32 pairs
-// with integer operations; every certified result is written; the indices of
+// shared memory; each thread stages its next track's raw 64-bit words in shared
+// memory (cp.async) while it computes the current one, splits them into binary32
+// pairs with integer operations; every certified result is written; the indices of
 // the others are appended to a worklist (one atomicAdd per warp after a ballot).
 // Pass 2 (k_refine_fp64): the same binary64 evaluation as the plain FP64 pass,
 // over the worklist only; its length is read on the device, so the two launches
@@ -19,6 +20,17 @@ __device__ __forceinline__ void stage_desc32(Desc& dst, const Desc* __restrict__
   for (int i = threadIdx.x; i < (int)(sizeof(Desc) / 16); i += blockDim.x) d[i] = s[i];
 }
 
+// Asynchronous global -> shared copies (8 bytes each) that the issuing thread waits for
+// with cp.async.wait_group: a thread stages its next track while it computes the current
+// one, so the loads' latency overlaps the arithmetic without holding registers.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Block shape of the one-track-per-thread pass per family (box, trd/trap, tube, cone):
 // threads and resident blocks per SM, from the registers each family needs.
 template <int FAMILY> struct Shape32 { static constexpr int threads = 256, blocks = 3; };
@@ -29,24 +41,44 @@ template <int FAMILY>
 __global__ void __launch_bounds__(Shape32<FAMILY>::threads, Shape32<FAMILY>::blocks) k_query_fp32(const Desc* __restrict__ desc, QueryArgs a,
                                                     uint32_t* __restrict__ worklist,
                                                     unsigned long long* __restrict__ counter) {
+  constexpr int NT = Shape32<FAMILY>::threads;
   __shared__ Desc S;
+  __shared__ uint2 stage[2][6][NT];  // this thread's current and next track, raw words
   stage_desc32(S, desc);
   __syncthreads();
   const unsigned want = (a.inside ? f32::kWantCode : 0u) | (a.din ? f32::kWantDin : 0u) |
                         (a.dout ? f32::kWantDout : 0u) | (a.sin ? f32::kWantSin : 0u) |
                         (a.sout ? f32::kWantSout : 0u);
   const bool dirs = want & (f32::kWantDin | f32::kWantDout);
-  const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
-              *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
-              *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
+  const uint2* src[6] = {reinterpret_cast<const uint2*>(a.x), reinterpret_cast<const uint2*>(a.y),
+                         reinterpret_cast<const uint2*>(a.z), reinterpret_cast<const uint2*>(a.u),
+                         reinterpret_cast<const uint2*>(a.v), reinterpret_cast<const uint2*>(a.w)};
   const unsigned lane = threadIdx.x & 31u;
+  const unsigned tid = threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // stage the words of track i into buffer b (nothing for i beyond the basket); one commit
+  // group per call, so that wait_group<1> always means "all but the latest group landed"
+  auto prefetch = [&](int64_t i, int b) {
+    if (i < a.n) {
+#pragma unroll
+      for (int c = 0; c < 6; c++)
+        if (c < 3 || dirs) cp_async8(&stage[b][c][tid], src[c] + i);
+    }
+    cp_async_commit();
+  };
+  int buf = 0;
+  prefetch((int64_t)blockIdx.x * blockDim.x + tid, 0);
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
-    const int64_t i = base + threadIdx.x;
+    const int64_t i = base + tid;
+    prefetch(i + stride, buf ^ 1);
+    cp_async_wait<1>();
     const bool valid = i < a.n;
     bool flag = false;
     if (valid) {
-      const f32::TrackF T = f32::load_track<(FAMILY >= 2)>(X, Y, Z, Ux, Uy, Uz, i, dirs);
+      const uint2 zero{0u, 0u};
+      const f32::TrackF T = f32::track_from_words<(FAMILY >= 2)>(
+          stage[buf][0][tid], stage[buf][1][tid], stage[buf][2][tid], dirs ? stage[buf][3][tid] : zero,
+          dirs ? stage[buf][4][tid] : zero, dirs ? stage[buf][5][tid] : zero, dirs);
       f32::R32 R;
       R.flag = T.bad;
       R.code = 1;
@@ -74,7 +106,9 @@ __global__ void __launch_bounds__(Shape32<FAMILY>::threads, Shape32<FAMILY>::blo
       at = __shfl_sync(0xffffffffu, at, leader);
       if (flag) worklist[at + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
     }
+    buf ^= 1;
   }
+  cp_async_wait<0>();  // no copy outlives the block
 }
 
 // Results of one finished track: written when certified, else its index appended to

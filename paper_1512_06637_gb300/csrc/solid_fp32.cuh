@@ -117,22 +117,20 @@ __device__ __forceinline__ unsigned long long f2d_bits(float f) {
   return (unsigned long long)__double_as_longlong((double)f);
 }
 
+// A track from the raw binary64 words of its point and direction.
 template <bool DIR_LO = true>
-__device__ __forceinline__ TrackF load_track(const uint2* x, const uint2* y, const uint2* z,
-                                             const uint2* u, const uint2* v, const uint2* w,
-                                             int64_t i, bool dirs) {
+__device__ __forceinline__ TrackF track_from_words(uint2 bx, uint2 by, uint2 bz, uint2 bu, uint2 bv, uint2 bw,
+                                                   bool dirs) {
   TrackF T;
   T.bad = false;
   T.fl = FLOOR;
   T.dfl = 0.f;
   T.keyed = true;
-  const uint2 bz = __ldg(z + i);
-  split(__ldg(x + i), T.xh, T.xl, T.bad);
-  split(__ldg(y + i), T.yh, T.yl, T.bad);
+  split(bx, T.xh, T.xl, T.bad);
+  split(by, T.yh, T.yl, T.bad);
   split(bz, T.zh, T.zl, T.bad);
   T.zkey = order_key((long long)(((unsigned long long)bz.y << 32) | bz.x));
   if (dirs) {
-    const uint2 bu = __ldg(u + i), bv = __ldg(v + i), bw = __ldg(w + i);
     T.u = trunc_hi(bu, T.bad);
     T.v = trunc_hi(bv, T.bad);
     T.w = trunc_hi(bw, T.bad);
@@ -150,6 +148,15 @@ __device__ __forceinline__ TrackF load_track(const uint2* x, const uint2* y, con
     T.ul = T.vl = T.wl = 0.f;
   }
   return T;
+}
+
+template <bool DIR_LO = true>
+__device__ __forceinline__ TrackF load_track(const uint2* x, const uint2* y, const uint2* z,
+                                             const uint2* u, const uint2* v, const uint2* w,
+                                             int64_t i, bool dirs) {
+  const uint2 zero{0u, 0u};
+  return track_from_words<DIR_LO>(__ldg(x + i), __ldg(y + i), __ldg(z + i), dirs ? __ldg(u + i) : zero,
+                                  dirs ? __ldg(v + i) : zero, dirs ? __ldg(w + i) : zero, dirs);
 }
 
 // ------------------------------------------------- double-float pieces
@@ -744,14 +751,35 @@ __device__ inline bool pcon_begin(const Desc& S, const TrackF& T, unsigned want,
           if (has_phi) { v = fmaxf(v, gphi); e += phhi - phlo; }
           return v;
         };
-        float umin = F_INF;
-        for (int k = 0; k < last; k++) {
+        // Sections are visited outward from k0 in z: a piece's value is at least its z-gap
+        // (how far the point lies beyond the piece's z-slab), which grows away from k0, so
+        // once a gap minus its rounding bound exceeds umin no farther piece can hold the
+        // minimum (its exact value exceeds umin, an upper bound on the minimum).
+        auto far_in_z = [&](int k, float u) -> bool {
+          const float gap = fmaxf(S.zh[k] - T.zh, T.zh - S.zh[k + 1]);
+          return gap - fmaf(4.f * U, fabsf(T.zh) + fabsf(S.zh[k]) + fabsf(S.zh[k + 1]), T.fl) > u;
+        };
+        float umin;
+        {
+          float e;
+          const float v = closed_f(k0, e);
+          umin = v + e;
+        }
+        int klo = k0, khi = k0;
+        for (int k = k0 - 1; k >= 0 && !far_in_z(k, umin); k--) {
           float e;
           const float v = closed_f(k, e);
           umin = fminf(umin, v + e);
+          klo = k;
+        }
+        for (int k = k0 + 1; k < last && !far_in_z(k, umin); k++) {
+          float e;
+          const float v = closed_f(k, e);
+          umin = fminf(umin, v + e);
+          khi = k;
         }
         uint32_t cand = 0u;
-        for (int k = 0; k < last; k++) {
+        for (int k = klo; k <= khi; k++) {
           float e;
           const float v = closed_f(k, e);
           if (!(v - e > umin)) cand |= 1u << k;
