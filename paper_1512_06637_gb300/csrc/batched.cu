@@ -633,6 +633,7 @@ gv_status gv_batch_get_config(const gv_batch* b, gv_batch_config* c) {
 }
 
 gv_status gv_batch_run(gv_batch* b, const gv_tracks* t, gv_precision prec, const gv_results* r, void* stream) {
+  const gv::Range range("gv_batch_run");
   if (!b) return set_error(GV_ERR_INVALID_ARG, "batch: NULL handle");
   if (prec != GV_FP64 && prec != GV_FP32_REFINE) return set_error(GV_ERR_INVALID_ARG, "unknown precision");
   QueryArgs a;
@@ -667,6 +668,7 @@ gv_status gv_batch_refined(gv_batch* b, void* stream, int64_t* n) {
 // new results are appended.
 gv_status gv_batch_autotune(gv_batch* b, const gv_tracks* t, gv_precision prec, const gv_results* r, void* stream,
                             gv_batch_config* best_out) {
+  const gv::Range range("gv_batch_autotune");
   if (!b) return set_error(GV_ERR_INVALID_ARG, "batch: NULL handle");
   QueryArgs a;
   gv_status st = batch_args(b, t, r, a);

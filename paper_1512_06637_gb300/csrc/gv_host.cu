@@ -227,6 +227,7 @@ gv_status gv_workspace_refined(gv_workspace* w, void* stream, int64_t* n_refined
 
 gv_status gv_query(const gv_solid* s, const gv_tracks* t, gv_precision prec, const gv_results* res,
                    gv_workspace* ws, void* stream) {
+  const gv::Range range("gv_query");
   if (!s || !t || !res) return set_error(GV_ERR_INVALID_ARG, "NULL solid, tracks or results");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "negative track count");
   if (prec != GV_FP64 && prec != GV_FP32_REFINE) return set_error(GV_ERR_INVALID_ARG, "unknown precision");

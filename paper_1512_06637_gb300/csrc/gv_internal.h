@@ -1,6 +1,7 @@
 // gv_internal.h -- host-side internals shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string>
 #include <vector>
@@ -32,6 +33,15 @@ struct QueryArgs {
 };
 
 gv_status set_error(gv_status st, const std::string& msg);
+
+// An NVTX range around one call of the C ABI (visible to a profiler's timeline; a no-op
+// unless a tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Records of a device table of solids (a batch's or a geometry's): one per solid, then the
 // two component records of every boolean, whose parts pointer is set to them, so that the

@@ -116,6 +116,7 @@ void gv_pipeline_destroy(gv_pipeline* p) {
 
 gv_status gv_query_host(const gv_solid* s, const gv_tracks* t, gv_precision prec, const gv_results* res,
                         gv_pipeline* p, void* stream) {
+  const gv::Range range("gv_query_host");
   if (!s || !t || !res || !p) return set_error(GV_ERR_INVALID_ARG, "NULL solid, tracks, results or pipeline");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "negative track count");
   if (prec != GV_FP64 && prec != GV_FP32_REFINE) return set_error(GV_ERR_INVALID_ARG, "unknown precision");

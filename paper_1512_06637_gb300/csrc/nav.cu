@@ -1189,6 +1189,7 @@ static gv::Vox vox_of(const gv_geom* g) {
 }
 
 gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* t, int32_t* node, void* stream) {
+  const gv::Range range("gv_nav_locate");
   if (!g || !t) return set_error(GV_ERR_INVALID_ARG, "locate: NULL geometry or tracks");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "locate: negative track count");
   if (t->n == 0) return GV_OK;
@@ -1202,6 +1203,7 @@ gv_status gv_nav_locate(const gv_geom* g, const gv_tracks* t, int32_t* node, voi
 
 gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node, gv_precision prec, double* step,
                       double* safety, int32_t* next, gv_workspace* ws, void* stream) {
+  const gv::Range range("gv_nav_step");
   if (!g || !t) return set_error(GV_ERR_INVALID_ARG, "nav: NULL geometry or tracks");
   if (prec != GV_FP64 && prec != GV_FP32_REFINE) return set_error(GV_ERR_INVALID_ARG, "unknown precision");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "nav: negative track count");
@@ -1241,6 +1243,7 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
 gv_status gv_transport(const gv_geom* g, const gv_tracks* t, const int32_t* node0, const int32_t* node_material,
                        const double* sigma_n, int32_t nmat, const double* xi, int32_t kmax, gv_precision prec,
                        const gv_transport_out* out, void* stream) {
+  const gv::Range range("gv_transport");
   if (!g || !t || !out) return set_error(GV_ERR_INVALID_ARG, "transport: NULL geometry, tracks or outputs");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "transport: negative track count");
   if (kmax < 1 || nmat < 1) return set_error(GV_ERR_INVALID_ARG, "transport: kmax and nmat must be >= 1");

@@ -66,6 +66,7 @@ using namespace gv;
 
 extern "C" gv_status gv_query_fp32_static(const gv_solid* s, const gv_tracks* t, const gv_results* res,
                                           void* stream) {
+  const gv::Range range("gv_query_fp32_static");
   if (!s || !t || !res) return set_error(GV_ERR_INVALID_ARG, "gv_query_fp32_static: NULL solid, tracks or results");
   if (t->n < 0) return set_error(GV_ERR_INVALID_ARG, "gv_query_fp32_static: negative track count");
   if (t->n > kStaticMaxTracks)

@@ -159,6 +159,7 @@ static void ring_free_head(gv_server* s, const Group& g) {
 }
 
 static gv_status issue_group(gv_server* s, std::vector<int64_t>& tickets, int64_t total, int64_t off) {
+  const gv::Range range("gv_server group");
   const int si = s->next_stream;
   s->next_stream = (s->next_stream + 1) % s->cfg.streams;
   cudaStream_t st = s->streams[si];
@@ -327,6 +328,7 @@ gv_status gv_server_create(const gv_geom* g, const gv_server_config* cfg, gv_ser
 }
 
 gv_status gv_server_submit(gv_server* s, int64_t n, const double* host_in, void* host_out, int64_t* ticket) {
+  const gv::Range range("gv_server_submit");
   if (!s || !ticket || n < 0 || (n > 0 && (!host_in || !host_out)))
     return set_error(GV_ERR_INVALID_ARG, "server submit: bad arguments");
   if (group_bytes(n) > s->arena_bytes)

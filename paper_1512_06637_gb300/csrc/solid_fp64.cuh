@@ -71,6 +71,14 @@ struct Motion {
 };
 // A constraint the ray slides along: within the band, running along its surface.
 __device__ __forceinline__ bool slides(double g, int m) { return fabs(g) <= H && m == 0; }
+// The motion of a wall, computed only for a wall within the band (|g| <= h): elsewhere neither
+// the surface-start rule nor sliding looks at it (-1 stands in), and the division is skipped.
+__device__ __forceinline__ int wall_motion_near(double g, const Line& L, const Track& T, double r, double radial,
+                                                bool outer) {
+  if (!(fabs(g) <= H)) return -1;
+  const double gd = wall_gd(L, T, r, radial);
+  return wall_motion(outer ? gd : -gd, T, r, outer);
+}
 
 __device__ __forceinline__ void finish_safety(int code, double s_out_side, double s_in_side,
                                               Result& R) {
@@ -376,11 +384,11 @@ __device__ inline void pcon_query(const Desc& S, const Track& T, unsigned want, 
   Motion m;
   unsigned sl = 0;
   {
-    const int mo = wall_motion(wall_gd(S.out[k0], T, r, radial), T, r, true);
+    const int mo = wall_motion_near(go, S.out[k0], T, r, radial, true);
     m.add(go, mo);
     if (slides(go, mo)) sl |= kSlOut;
     if (inner_has(S, k0)) {
-      const int mi = wall_motion(-wall_gd(S.in[k0], T, r, radial), T, r, false);
+      const int mi = wall_motion_near(gi, S.in[k0], T, r, radial, false);
       m.add(gi, mi);
       if (slides(gi, mi)) sl |= kSlIn;
     }
@@ -612,10 +620,12 @@ __device__ __forceinline__ int minus(double lo, double hi, double xlo, double xh
 // The sliding constraints of a polycone-family primitive at the track's start.
 __device__ inline unsigned pcon_slides(const Desc& S, const Track& T, double r, double radial, int k0) {
   unsigned sl = 0;
-  if (slides(g_out(S.out[k0], r, T.z), wall_motion(wall_gd(S.out[k0], T, r, radial), T, r, true))) sl |= kSlOut;
-  if (inner_has(S, k0) &&
-      slides(g_in(S.in[k0], r, T.z), wall_motion(-wall_gd(S.in[k0], T, r, radial), T, r, false)))
-    sl |= kSlIn;
+  const double go = g_out(S.out[k0], r, T.z);
+  if (slides(go, wall_motion_near(go, S.out[k0], T, r, radial, true))) sl |= kSlOut;
+  if (inner_has(S, k0)) {
+    const double gi = g_in(S.in[k0], r, T.z);
+    if (slides(gi, wall_motion_near(gi, S.in[k0], T, r, radial, false))) sl |= kSlIn;
+  }
   if (slides(xsub(S.z[0], T.z), plane_motion(-T.w))) sl |= kSlZ0;
   if (slides(xsub(T.z, S.z[S.nz - 1]), plane_motion(T.w))) sl |= kSlZL;
   if (S.flags & kHasPhi) {
@@ -730,9 +740,12 @@ __device__ inline Start prim_start(const Desc& S, const Track& T) {
     const double r = __dsqrt_rn(xadd(xmul(T.x, T.x), xmul(T.y, T.y)));
     const int k0 = section_of(S, T.z);
     const double radial = xadd(xmul(T.x, T.u), xmul(T.y, T.v));
-    start_add(st, g_out(S.out[k0], r, T.z), wall_motion(wall_gd(S.out[k0], T, r, radial), T, r, true));
-    if (inner_has(S, k0))
-      start_add(st, g_in(S.in[k0], r, T.z), wall_motion(-wall_gd(S.in[k0], T, r, radial), T, r, false));
+    const double go = g_out(S.out[k0], r, T.z);
+    start_add(st, go, wall_motion_near(go, S.out[k0], T, r, radial, true));
+    if (inner_has(S, k0)) {
+      const double gi = g_in(S.in[k0], r, T.z);
+      start_add(st, gi, wall_motion_near(gi, S.in[k0], T, r, radial, false));
+    }
     start_add(st, xsub(S.z[0], T.z), plane_motion(-T.w));
     start_add(st, xsub(T.z, S.z[last]), plane_motion(T.w));
     if (S.flags & kHasPhi) {
