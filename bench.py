@@ -39,9 +39,17 @@ BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 double
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass); valid only while the kernel
 # sources hash to the value recorded with them, else the bench reports traffic = null.
 DRAM_CAPTURE = {
-    "sources_sha256": "126a20e9801ee15eab4c29e02b1cef2081b91b7ce4591619cbb36f5d64f8fcee",
-    "bytes_per_track": {'box': 79.01, 'trd': 78.98, 'tube': 79.30, 'cone': 79.44, 'polycone': 80.37},
+    "sources_sha256": "021ad82be26c546dcc2602f5e6a90387c680130b9553e7e3b35d8a352983dcec",
+    "bytes_per_track": {'box': 78.94, 'trd': 79.18, 'tube': 79.29, 'cone': 79.37, 'polycone': 80.19},
     "profile": "profiles/query_fp32_dram_full.md",
+}
+# Warp instructions per track of each binary32 pass (smsp__inst_executed.sum of one launch ÷
+# its tracks, from an ncu capture of the 2^21-track case; the counts do not depend on the
+# basket size), valid while the kernel sources hash to the recorded value.
+ISSUE_CAPTURE = {
+    "sources_sha256": "021ad82be26c546dcc2602f5e6a90387c680130b9553e7e3b35d8a352983dcec",
+    "warp_inst_per_track": {'box': 18.90, 'trd': 34.62, 'tube': 61.16, 'cone': 56.84, 'polycone': 116.34},
+    "profile": "profiles/query_fp32_issue_2M.md",
 }
 KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
 E2E_CHUNK = 1 << 22  # tracks per host-streaming chunk (2^19-2^22 measured: larger is faster)
@@ -365,14 +373,30 @@ def run_ours(args):
     peaks = load_peaks()
     achieved = n * BYTES_PER_TRACK / (dom_ms * 1e-3) / 1e9
     traffic = None
-    if precision == "fp32_refine" and kernel_sources_sha256() == DRAM_CAPTURE["sources_sha256"]:
+    sha = kernel_sources_sha256()
+    if precision == "fp32_refine" and sha == DRAM_CAPTURE["sources_sha256"]:
         per_track = DRAM_CAPTURE["bytes_per_track"].get(dom)
         traffic = None if per_track is None else per_track * n
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": f"query pass ({precision}) on {dom}", "peak_source": peaks["source"],
-                "traffic_source": DRAM_CAPTURE["profile"] if traffic is not None else
-                "none: the kernel sources changed since the last DRAM capture"}
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+           "kernel": f"query pass ({precision}) on {dom}", "peak_source": peaks["source"],
+           "traffic_source": DRAM_CAPTURE["profile"] if traffic is not None else
+           "none: the kernel sources changed since the last DRAM capture"}
+    # the same launch against the measured warp-instruction issue peak (these passes are
+    # issue-bound: the one whose fraction is larger binds)
+    alu = bench_alu_peaks(torch, local)
+    issue = None
+    if precision == "fp32_refine" and sha == ISSUE_CAPTURE["sources_sha256"] and dom in ISSUE_CAPTURE["warp_inst_per_track"]:
+        inst_rate = ISSUE_CAPTURE["warp_inst_per_track"][dom] * n / (dom_ms * 1e-3)
+        mhz = ck.get("sm_mhz") or alu["sm_mhz"]
+        ipeak = alu["issue_warp_inst_per_clk_per_sm"] * alu["sms"] * mhz * 1e6
+        issue = {"bound": "alu", "achieved": inst_rate, "peak": ipeak, "unit": "warp instructions/s",
+                 "frac": inst_rate / ipeak, "traffic": traffic, "kernel": hbm["kernel"],
+                 "peak_source": "measured (probe: binary32 multiply-add issue rate x SMs x sampled clock)",
+                 "instructions_source": ISSUE_CAPTURE["profile"]}
+    roofline = dict(issue if issue is not None and issue["frac"] > hbm["frac"] else hbm)
+    roofline["hbm_frac"] = hbm["frac"]
+    roofline["issue_frac"] = None if issue is None else issue["frac"]
 
     refined = None
     if ws is not None:
@@ -395,6 +419,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (4 GB per step)", "parallelism": f"replicas x{world}"},
         "per_solid_ms": per_solid_ms,
         "roofline": roofline,
+        "alu_peaks": alu,
         "clocks": ck,
         "gpu_launches": args.steps * len(names) * launches_per_query,
         "e2e": e2e,
