@@ -1,7 +1,7 @@
 """The device transport loop (gv_transport) against the oracle's loop on the same tracks,
 materials and random numbers: end reason, number of steps and last volume identical and end
-point and path length within 1e-7 mm for every track that neither side marks as hanging on a
-near tie; ties are rare; edge cases (one step allowed, tracks starting outside the world,
+point and path length within 1e-9 mm (+1e-12 relative) for every track that neither side marks
+as hanging on a near tie; ties are rare; edge cases (one step allowed, tracks starting outside the world,
 vacuum everywhere, a material index out of range)."""
 import numpy as np
 import pytest
@@ -42,14 +42,23 @@ def run_both(gv, geo, tr, node0, mat, sig, xi, kmax, with_oracle=True):
     return got, want
 
 
-def check(got, want, tol=1e-7):
+def check(got, want, tol=1e-9):
+    """End reason, step count and last volume identical; end point and path within 1e-9 mm plus
+    1e-12 of their magnitude.  Derivation: on a track that neither side marks as a near tie both
+    take the same decisions, and each step's length is a binary64 distance that the two sides
+    form with different operations, so they differ by a few units in the last place of
+    quantities below 1.2e3 mm (about 1e-12 mm); over at most 64 steps those differences add up
+    to below 1e-10 mm."""
     sure = (got["tie"] == 0) & (want["tie"] == 0)
     for k in ("reason", "steps", "last"):
         bad = np.nonzero(sure & (got[k] != want[k]))[0]
         assert len(bad) == 0, (k, bad[:5], got[k][bad[:5]], want[k][bad[:5]])
+    worst = 0.0
     for k in ("x", "y", "z", "path"):
         err = np.abs(got[k] - want[k])[sure]
-        assert (err <= tol + 1e-9 * np.abs(want[k][sure])).all(), (k, err.max())
+        assert (err <= tol + 1e-12 * np.abs(want[k][sure])).all(), (k, err.max())
+        worst = max(worst, float(err.max()) if err.size else 0.0)
+    print(f"largest end point / path difference: {worst:.3e} mm")
     return 1.0 - sure.mean()
 
 

@@ -141,6 +141,9 @@ def test_voxel_transport(gv, crowded):
     assert sure.mean() > 0.98
     for k in ("reason", "steps", "last"):
         assert np.array_equal(on[k][:m][sure], want[k][sure]), k
-    for k in ("x", "y", "z", "path"):
+    worst = 0.0
+    for k in ("x", "y", "z", "path"):  # the transport test's bound: 1e-9 mm + 1e-12 relative
         err = np.abs(on[k][:m][sure] - want[k][sure])
-        assert (err <= 1e-7 + 1e-9 * np.abs(want[k][sure])).all(), (k, err.max())
+        assert (err <= 1e-9 + 1e-12 * np.abs(want[k][sure])).all(), (k, err.max())
+        worst = max(worst, float(err.max()))
+    print(f"largest end point / path difference: {worst:.3e} mm")
