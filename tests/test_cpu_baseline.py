@@ -35,3 +35,10 @@ def test_cpu_baseline_random_solids(i):
 def test_cpu_baseline_grazing(fam):
     spec, tr, _ = W.grazing_tracks(fam, 4000, 700 + W.GRAZING_FAMILIES.index(fam))
     compare(*_both(spec, tr), "fp64", fam)
+
+
+@pytest.mark.parametrize("i", range(len(W.degenerate_table())))
+def test_cpu_baseline_degenerate(i):
+    spec = W.degenerate_table()[i]
+    tr = W.tracks_for_solid(spec, 20011, seed=800 + i)
+    compare(*_both(spec, tr), "fp64", f"degenerate {spec['kind']}#{i}")

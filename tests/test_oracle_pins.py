@@ -412,6 +412,161 @@ def test_brute_force_ray_march(idx):
     assert agree_x.mean() >= 0.985, agree_x.mean()
 
 
+DEGEN = W.degenerate_table()
+
+
+@pytest.mark.parametrize("idx", [0, 1, 3, 7, 8, 11])
+def test_degenerate_solids_brute_force(idx):
+    """Solids at the edges of their parameter ranges (32 planes with walls pinching to the axis,
+    phi wedges of 1e-3 rad, exactly pi and just below 2 pi, apex cones, a 60-degree trap):
+    ray marching with bisection on the tolerance-free s agrees with the distances."""
+    spec = DEGEN[idx]
+    s = sol(spec)
+    n = 300
+    t = W.tracks_for_solid(spec, n, seed=900 + idx, near_frac=0.0)
+    P = np.stack([t["x"], t["y"], t["z"]], 1)
+    D = np.stack([t["dx"], t["dy"], t["dz"]], 1)
+    r = s.query(**t)
+    hb = W.bounding_half(spec)
+    tmax = 2.0 * np.linalg.norm(hb * 2.0 + 1.0)
+    step = float(max(hb.min() / 400.0, 0.002))
+    out, ins = r["inside"] == OUT, r["inside"] == IN
+    te = _march(s, P[out], D[out], True, tmax, step)
+    tx = _march(s, P[ins], D[ins], False, tmax, step)
+    got_e, got_x = r["dist_in"][out], r["dist_out"][ins]
+    fin = np.isfinite(te)
+    assert (got_e[fin] <= te[fin] + 1e-9).all()
+    with np.errstate(invalid="ignore"):
+        agree_e = np.where(fin, np.abs(got_e - te) <= 1e-9, np.isinf(got_e))
+    agree_x = np.abs(got_x - tx) <= 1e-9
+    assert agree_e.mean() >= 0.97, agree_e.mean()
+    assert agree_x.mean() >= 0.97, agree_x.mean()
+
+
+def test_degenerate_thin_wedge_march():
+    """A tube segment 1e-3 rad wide: chords across it are about 0.01 mm, so the march steps
+    0.002 mm (on fewer rays); it agrees with the distances."""
+    spec = DEGEN[2]
+    s = sol(spec)
+    t = W.tracks_for_solid(spec, 60, seed=902, near_frac=0.0)
+    P = np.stack([t["x"], t["y"], t["z"]], 1)
+    D = np.stack([t["dx"], t["dy"], t["dz"]], 1)
+    r = s.query(**t)
+    out, ins = r["inside"] == OUT, r["inside"] == IN
+    te = _march(s, P[out], D[out], True, 130.0, 0.002)
+    tx = _march(s, P[ins], D[ins], False, 130.0, 0.002)
+    fin = np.isfinite(te)
+    with np.errstate(invalid="ignore"):
+        agree_e = np.where(fin, np.abs(r["dist_in"][out] - te) <= 1e-9, np.isinf(r["dist_in"][out]))
+    assert agree_e.all(), agree_e.mean()
+    assert (np.abs(r["dist_out"][ins] - tx) <= 1e-9).all()
+
+
+def test_degenerate_sliver_exit():
+    """A tube segment of 2 pi - 1e-9 from phi = 1 rad: the excluded sliver lies between the
+    half-planes phi = 1 - 1e-9 and phi = 1, so a ray from inside leaves at the first of: either
+    half-plane (crossed at r > 0), r = 20, r = 5 (into the hole), the end planes z = +/-30."""
+    spec = DEGEN[4]
+    s = sol(spec)
+    g = np.random.default_rng(74)
+    n = 4000
+    rr = g.uniform(5.5, 19.5, n)
+    ph = 1.0 + g.uniform(0.01, 2 * math.pi - 0.01, n)
+    z = g.uniform(-29, 29, n)
+    p = np.stack([rr * np.cos(ph), rr * np.sin(ph), z], 1)
+    d = W.isotropic(n, g)
+    r = s.query(p[:, 0], p[:, 1], p[:, 2], d[:, 0], d[:, 1], d[:, 2])
+    assert (r["inside"] == IN).all()
+    edges = [np.array([math.cos(a), math.sin(a)]) for a in (1.0, 1.0 + (2 * math.pi - 1e-9))]
+    for i in range(n):
+        x, y, zz = p[i]
+        u, v, w = d[i]
+        cands = []
+        A, B = u * u + v * v, x * u + y * v
+        for R, hole in ((20.0, False), (5.0, True)):
+            C = x * x + y * y - R * R
+            disc = B * B - A * C
+            if A > 0 and disc > 0:
+                t1, t2 = (-B - math.sqrt(disc)) / A, (-B + math.sqrt(disc)) / A
+                cands.append(t1 if hole else t2)  # into the hole at its first root, out of r = 20 at the second
+        if w != 0:
+            cands.append(((30.0 if w > 0 else -30.0) - zz) / w)
+        for e in edges:  # crossing of the line through the axis along e, on e's side
+            den = e[1] * u - e[0] * v
+            if den != 0:
+                t = -(e[1] * x - e[0] * y) / den
+                qx, qy = x + t * u, y + t * v
+                if t > 0 and qx * e[0] + qy * e[1] > 0:
+                    cands.append(t)
+        want = min(c for c in cands if c > 0)
+        assert r["dist_out"][i] == pytest.approx(want, rel=1e-9, abs=1e-9), (i, r["dist_out"][i], want)
+
+
+@pytest.mark.parametrize("idx", [9, 10])
+def test_degenerate_boxes_slab(idx):
+    """A box 1e-3 mm wide and one 5000 x 1 x 5000 mm: the slab method."""
+    D = np.array(DEGEN[idx]["params"])
+    b = sol(DEGEN[idx])
+    g = np.random.default_rng(60 + idx)
+    n = 5000
+    p = g.uniform(-1, 1, (n, 3)) * 2 * D
+    d = W.isotropic(n, g)
+    r = b.query(p[:, 0], p[:, 1], p[:, 2], d[:, 0], d[:, 1], d[:, 2])
+    for i in range(n):
+        tn, tf = _slab(D, p[i], d[i])
+        if r["inside"][i] == IN:
+            assert r["dist_out"][i] == pytest.approx(tf, rel=1e-12, abs=1e-12)
+        elif r["inside"][i] == OUT:
+            want = tn if (tf - tn > 1e-12 and tn > 0) else np.inf
+            got = r["dist_in"][i]
+            assert (np.isinf(want) and np.isinf(got)) or got == pytest.approx(want, rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("idx", [5, 6])
+def test_degenerate_tubes_closed_form(idx):
+    """A shell 1e-6 mm thick at r = 10 and a cylinder 3 mm wide and 10 m long (full phi): the
+    first crossing of r = rmax (from outside) or r = rmin (from the hole) or of the end planes,
+    from the cylinder quadratic."""
+    rmin, rmax, dz = DEGEN[idx]["params"][:3]
+    c = sol(DEGEN[idx])
+    g = np.random.default_rng(70 + idx)
+    n = 5000
+    zr = min(2 * dz, 100.0)
+    p = np.stack([g.uniform(-2, 2, n) * rmax, g.uniform(-2, 2, n) * rmax, g.uniform(-1, 1, n) * zr], 1)
+    d = W.isotropic(n, g)
+    r = c.query(p[:, 0], p[:, 1], p[:, 2], d[:, 0], d[:, 1], d[:, 2])
+
+    def roots(R, x, y, u, v):
+        A, B, C = u * u + v * v, x * u + y * v, x * x + y * y - R * R
+        disc = B * B - A * C
+        if A == 0 or disc <= 0:
+            return None
+        sq = math.sqrt(disc)
+        return (-B - sq) / A, (-B + sq) / A
+
+    checked = 0
+    for i in range(n):
+        if r["inside"][i] != OUT:
+            continue
+        x, y, z = p[i]
+        u, v, w = d[i]
+        rr = math.hypot(x, y)
+        if abs(z) >= dz or abs(rr - rmax) < 1e-3 or abs(rr - rmin) < 1e-3:
+            continue  # entries through the end planes and near-surface starts: other pins
+        if rr > rmax:
+            q = roots(rmax, x, y, u, v)
+            want = q[0] if q is not None and q[0] > 0 else np.inf
+        else:  # in the hole
+            q = roots(rmin, x, y, u, v)
+            want = q[1]
+        if np.isfinite(want) and abs(z + want * w) >= dz:
+            continue
+        got = r["dist_in"][i]
+        assert (np.isinf(want) and np.isinf(got)) or got == pytest.approx(want, rel=1e-9, abs=1e-9), (i, got, want)
+        checked += 1
+    assert checked > 500
+
+
 # ------------------------------------------------------------ grazing rays
 #
 # Rays that touch a surface, run along it, or pass exactly through an edge (the VecGeom

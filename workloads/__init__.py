@@ -651,3 +651,32 @@ def grazing_tracks(family: str, n: int, seed: int):
         d = np.stack([dxy[:, 0], dxy[:, 1], zero], 1)
         return spec, soa(p, d), {"out": out}
     raise ValueError(family)
+
+
+# ------------------------------------------------------------ degenerate solids
+
+def degenerate_table() -> list[dict]:
+    """Solids at the edges of their parameter ranges: the largest polycone (32 planes, walls
+    pinching to the axis), phi wedges of 1e-3 rad, exactly pi and just below 2 pi, a wall 1e-6 mm
+    thick, cones whose outer radius shrinks to 1e-3 mm at one end, a tube 1e4 mm long, a box 1e-3 mm
+    wide, and a trap tilted 60 degrees."""
+    g = rng(4242)
+    z = np.sort(g.uniform(-80.0, 80.0, 32))
+    z = z + np.arange(32) * 1e-3  # strictly increasing
+    rmax = g.uniform(5.0, 40.0, 32)
+    rmin = np.where(g.random(32) < 0.3, 0.0, rmax * g.uniform(0.1, 0.9, 32))
+    return [
+        {"kind": "polycone", "params": (tuple(z), tuple(rmin), tuple(rmax), 0.0, TWO_PI)},
+        {"kind": "polycone", "params": (tuple(z), tuple(rmin), tuple(rmax), 0.4, 4.0)},
+        {"kind": "tube", "params": (5.0, 20.0, 30.0, 0.3, 1e-3)},
+        {"kind": "tube", "params": (5.0, 20.0, 30.0, 0.3, math.pi)},
+        {"kind": "tube", "params": (5.0, 20.0, 30.0, 1.0, TWO_PI - 1e-9)},
+        {"kind": "tube", "params": (10.0, 10.0 + 1e-6, 30.0, 0.0, TWO_PI)},
+        {"kind": "tube", "params": (0.0, 3.0, 5000.0, 0.0, TWO_PI)},
+        {"kind": "cone", "params": (0.0, 1e-3, 0.0, 20.0, 30.0, 0.0, TWO_PI)},
+        {"kind": "cone", "params": (2.0, 20.0, 0.0, 1e-3, 30.0, 0.5, 2.0)},
+        {"kind": "box", "params": (1e-3, 1e-3, 1e-3)},
+        {"kind": "box", "params": (5000.0, 1.0, 5000.0)},
+        {"kind": "trap", "params": ((20.0, 60.0 * DEG, 30.0 * DEG, 10.0, 5.0, 8.0, 20.0 * DEG, 10.0, 5.0, 8.0, 20.0 * DEG),)},
+    ]
+
