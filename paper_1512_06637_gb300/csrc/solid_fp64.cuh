@@ -224,9 +224,11 @@ __device__ __forceinline__ double phi_g(const Desc& S, const Phi& f) {
 // Sliding constraints of a polycone-family track (bits), its start section k0.
 enum : unsigned { kSlOut = 1, kSlIn = 2, kSlZ0 = 4, kSlZL = 8, kSlPs = 16, kSlPe = 32 };
 
-// Entry checks.  An entry at t through one surface counts when the ray is then inside
-// every other constraint for longer than kMerge: g + kMerge max(g', 0) < 0 at the entry
-// point (a shorter chord is a touch).  A sliding constraint never holds the interior.
+// Entry checks.  An entry at t through one surface counts when the ray is inside every other
+// constraint at t + kMerge: g + kMerge g' < 0 at the entry point.  A constraint left within
+// kMerge of t gives a chord shorter than kMerge (a touch); one entered within kMerge of t is
+// entered at the same crossing (crossings closer than kMerge merge).  A sliding constraint
+// never holds the interior.
 struct Entry {
   double u, v, w;     // direction
   double nds, nde;    // phi normals . d
@@ -236,14 +238,14 @@ struct Entry {
 // Phi membership of an entry point.
 __device__ __forceinline__ bool phi_ok(const Desc& S, const Entry& E, double x, double y) {
   if (!(S.flags & kHasPhi)) return true;
-  const bool a_ok = !(E.sl & kSlPs) && xadd(xadd(xmul(S.ns[0], x), xmul(S.ns[1], y)), kMerge * dmax(E.nds, 0.0)) < 0;
-  const bool b_ok = !(E.sl & kSlPe) && xadd(xadd(xmul(S.ne[0], x), xmul(S.ne[1], y)), kMerge * dmax(E.nde, 0.0)) < 0;
+  const bool a_ok = !(E.sl & kSlPs) && xadd(xadd(xmul(S.ns[0], x), xmul(S.ns[1], y)), kMerge * E.nds) < 0;
+  const bool b_ok = !(E.sl & kSlPe) && xadd(xadd(xmul(S.ne[0], x), xmul(S.ne[1], y)), kMerge * E.nde) < 0;
   return (S.flags & kPhiWide) ? (a_ok || b_ok) : (a_ok && b_ok);
 }
 // Between the end planes at an entry point.
 __device__ __forceinline__ bool zends_ok(const Desc& S, const Entry& E, double z) {
   const int last = S.nz - 1;
-  return xsub(z, S.z[0]) > kMerge * dmax(-E.w, 0.0) && xsub(S.z[last], z) > kMerge * dmax(E.w, 0.0);
+  return xsub(z, S.z[0]) > kMerge * -E.w && xsub(S.z[last], z) > kMerge * E.w;
 }
 
 __device__ __forceinline__ int section_of(const Desc& S, double z) {
@@ -296,7 +298,7 @@ __device__ inline Cross line_cross(const Line& L, const Track& T, double r2, dou
 __device__ __forceinline__ bool inner_has(const Desc& S, int k) { return (S.inner >> k) & 1u; }
 
 // Lateral membership of an entry point in section k (skip_out / skip_in: the surface
-// entered through), with the entry margin: (r^2 - R^2) + 2 kMerge max(d(r^2 - R^2)/dt, 0) < 0
+// entered through), with the entry margin: (r^2 - R^2) + 2 kMerge d(r^2 - R^2)/dt / 2 < 0
 // for the outer wall and the reverse for the inner one.  The walls of the start section
 // slide when their bit is set: never inside there.
 __device__ __forceinline__ bool radial_ok(const Desc& S, const Entry& E, int k, double x, double y, double z,
@@ -305,12 +307,12 @@ __device__ __forceinline__ bool radial_ok(const Desc& S, const Entry& E, int k, 
   if (!skip_out) {
     if (k == E.k0 && (E.sl & kSlOut)) return false;
     const double R = S.out[k].a * z + S.out[k].b;
-    if (!(R > 0 && (r2 - R * R) + 2 * kMerge * dmax(rd - R * (S.out[k].a * E.w), 0.0) < 0)) return false;
+    if (!(R > 0 && (r2 - R * R) + 2 * kMerge * (rd - R * (S.out[k].a * E.w)) < 0)) return false;
   }
   if (!skip_in && inner_has(S, k)) {
     if (k == E.k0 && (E.sl & kSlIn)) return false;
     const double R = S.in[k].a * z + S.in[k].b;
-    if (R >= 0 && !((r2 - R * R) - 2 * kMerge * dmax(R * (S.in[k].a * E.w) - rd, 0.0) > 0)) return false;
+    if (R >= 0 && !((r2 - R * R) - 2 * kMerge * (R * (S.in[k].a * E.w) - rd) > 0)) return false;
   }
   return true;
 }
@@ -523,7 +525,7 @@ __device__ inline void pcon_query(const Desc& S, const Track& T, unsigned want, 
           if (!wide) {  // inside the other plane
             const double* n2 = j == 0 ? S.ne : S.ns;
             const double nd2 = j == 0 ? nde : nds;
-            if (!(xadd(xadd(xmul(n2[0], qx), xmul(n2[1], qy)), kMerge * dmax(nd2, 0.0)) < 0)) continue;
+            if (!(xadd(xadd(xmul(n2[0], qx), xmul(n2[1], qy)), kMerge * nd2) < 0)) continue;
           }
           best = t;
         }

@@ -159,3 +159,11 @@ def test_fp32_grazing(gv, fam):
     spec, tr, _ = W.grazing_tracks(fam, 4000, 700 + W.GRAZING_FAMILIES.index(fam))
     got, refined = run32(gv, spec, tr)
     compare(got, oracle.Solid.from_spec(spec).query(**tr), "fp32", fam)
+
+@pytest.mark.parametrize("i", range(len(W.degenerate_table())))
+def test_fp32_degenerate_solids(gv, i):
+    """The degenerate solids through the binary32 pass and its refinement."""
+    spec = W.degenerate_table()[i]
+    tr = W.tracks_for_solid(spec, 20011, seed=800 + i)
+    got, refined = run32(gv, spec, tr)
+    compare(got, oracle.Solid.from_spec(spec).query(**tr), "fp32", f"degenerate {spec['kind']}#{i}")

@@ -157,3 +157,12 @@ def test_fp64_cone_axis_apex(gv):
     d = np.stack([np.zeros(n), np.zeros(n), np.where(g.random(n) < 0.5, 1.0, -1.0)], 1)
     got, want = run_both(gv, W.CONE_M2, W.soa(p, d))
     compare(got, want, "fp64", "cone-axis")
+
+@pytest.mark.parametrize("i", range(len(W.degenerate_table())))
+def test_fp64_degenerate_solids(gv, i):
+    """Solids at the edges of their parameter ranges (32 planes, phi wedges of 1e-3 rad, exactly
+    pi and just below 2 pi, a 1e-6 mm wall, apex cones, 1e-3 mm and 1e4 mm solids, a 60-degree trap)."""
+    spec = W.degenerate_table()[i]
+    tr = W.tracks_for_solid(spec, 20011, seed=800 + i)
+    got, want = run_both(gv, spec, tr)
+    compare(got, want, "fp64", f"degenerate {spec['kind']}#{i}")
