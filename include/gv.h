@@ -59,7 +59,9 @@ enum { GV_INSIDE = 0, GV_SURFACE = 1, GV_OUTSIDE = 2 };
  * cannot certify (codes near the surface band, ill-conditioned roots, short
  * distances) and recomputes exactly those tracks in binary64.  Codes are
  * identical to GV_FP64; distances and safeties agree to 1e-5 relative
- * (1e-9 mm absolute below 1e-4 mm). */
+ * (1e-9 mm absolute below 1e-4 mm).  Booleans, and solids with a feature finer
+ * than 2^-16 of their size (a wall, a z-section, a phi wedge, or the sliver a
+ * phi segment leaves out), are evaluated in binary64 under both. */
 typedef enum { GV_FP64 = 0, GV_FP32_REFINE = 1 } gv_precision;
 
 #define GV_MAX_ZPLANES 32 /* largest polycone z-plane count */
@@ -377,6 +379,17 @@ void gv_server_destroy(gv_server* s);
  * arguments and errors otherwise as for gv_query with GV_FP32_REFINE. */
 gv_status gv_query_fp32_static(const gv_solid* s, const gv_tracks* tracks, const gv_results* res,
                                void* stream);
+
+/* Device-side checks of a GV_DEBUG build (the paper has no counterpart: a development aid).
+ * A library built with GV_DEBUG=1 (libgvgeo_debug.so) checks on the device, in the query passes,
+ * that directions are unit vectors (| |d|^2 - 1 | <= 1e-6), that a refinement worklist holds no
+ * more entries than its basket and that every track it names exists; a failed check records its
+ * code and the smallest offending track index, and the pass goes on.  gv_debug_status
+ * synchronises the device and returns the OR of the codes seen (*codes) and that index
+ * (*first_index, -1 if none) since the last clear; clear != 0 resets them.  A release build
+ * returns GV_ERR_UNSUPPORTED (codes 0, index -1). */
+enum { GV_DEBUG_DIRECTION = 1, GV_DEBUG_WORKLIST = 2, GV_DEBUG_INDEX = 4 };
+gv_status gv_debug_status(uint32_t* codes, int64_t* first_index, int32_t clear);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* gv_last_error(void);

@@ -9,7 +9,9 @@ import ctypes
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libgvgeo.so")
+# GV_DEBUG=1 selects the build with device-side checks (build.py, gv_debug_status)
+DEBUG = os.environ.get("GV_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(PKG, "libgvgeo_debug.so" if DEBUG else "libgvgeo.so")
 
 GV_OK, GV_ERR_INVALID_ARG, GV_ERR_UNSUPPORTED, GV_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
 GV_ERR_CUDA, GV_ERR_TIMEOUT, GV_ERR_BUSY = 4, 5, 6
@@ -101,6 +103,7 @@ SIGNATURES = {
     "gv_server_reset_stats": (_i, [_p]),
     "gv_server_destroy": (None, [_p]),
     "gv_query_fp32_static": (_i, [_p, ctypes.POINTER(Tracks), ctypes.POINTER(Results), _p]),
+    "gv_debug_status": (_i, [_p, _p, _i]),
     "gv_last_error": (ctypes.c_char_p, []),
     "gv_version": (ctypes.c_char_p, []),
 }

@@ -1,4 +1,5 @@
-"""Build the CUDA library ``libgvgeo.so`` in-tree for sm_103a.
+"""Build the CUDA library ``libgvgeo.so`` in-tree for sm_103a (with ``GV_DEBUG=1`` in the
+environment: ``libgvgeo_debug.so``, the build with device-side checks, objects in ``_build_debug/``).
 
 Each ``csrc/*.cu`` is compiled to an object in parallel with
 ``nvcc -gencode arch=compute_103a,code=sm_103a``; the objects are linked into
@@ -17,8 +18,9 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-OBJ = os.path.join(PKG, "_build")
-LIB = os.path.join(PKG, "libgvgeo.so")
+DEBUG = os.environ.get("GV_DEBUG", "0") not in ("", "0")  # the build with device-side checks
+OBJ = os.path.join(PKG, "_build_debug" if DEBUG else "_build")
+LIB = os.path.join(PKG, "libgvgeo_debug.so" if DEBUG else "libgvgeo.so")
 PROBE = os.path.join(PKG, "libgvprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -37,7 +39,7 @@ def flags() -> list[str]:
     # same arithmetic).
     return ARCH + ["-O3", "--fmad=false", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                    "-Xcompiler", "-ffp-contract=off", "-Xptxas", "-warn-spills",
-                   "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+                   "-I", os.path.join(ROOT, "include"), "-I", CSRC] + (["-DGV_DEBUG=1"] if DEBUG else [])
 
 
 def sources() -> list[str]:

@@ -125,6 +125,7 @@ template <> struct BShape<kFamBool> { static constexpr int threads = 256, blocks
 constexpr int kWalkTile = 32;
 
 int family_of(const Desc& h) {
+  if (h.flags & kFp64Only) return kFamBool;  // binary64 only, with the booleans
   switch (h.type) {
     case kBox: return kFamBox;
     case kTrd:
@@ -292,7 +293,8 @@ __global__ void __launch_bounds__(BShape<kFamWalk>::threads, BShape<kFamWalk>::b
   }
 }
 
-// Booleans: binary64 directly (no binary32 form), one track per thread.
+// Booleans and solids with features finer than binary32 resolves: binary64 directly, one
+// track per thread.
 __global__ void __launch_bounds__(BShape<kFamBool>::threads, BShape<kFamBool>::blocks)
     k_bbool64(const Desc* __restrict__ solids, const Tile* __restrict__ tiles, int ntiles, unsigned* __restrict__ next,
               QueryArgs a) {
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(BShape<kFamBool>::threads, BShape<kFamBool>::b
       f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
       if (want & 6u) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
       f64::Result R;
-      f64::bool_query(S, T, want, R);
+      f64::query(S, T, want, R);
       if (a.inside) a.inside[i] = (int8_t)R.code;
       if (a.din) a.din[i] = R.din;
       if (a.dout) a.dout[i] = R.dout;

@@ -87,6 +87,31 @@ inline void fill_f32(Desc& h) {
   h.size = size;
 }
 
+// Features finer than 2^-16 of the solid's size: binary64 only (kFp64Only).
+constexpr double kFineFeature = 1.0 / 65536.0;
+inline void mark_fine_features(Desc& h) {
+  if (h.type == kBox) {
+    const double big = std::fmax(h.D[0], std::fmax(h.D[1], h.D[2]));
+    if (std::fmin(h.D[0], std::fmin(h.D[1], h.D[2])) < kFineFeature * big) h.flags |= kFp64Only;
+    return;
+  }
+  if (h.type == kTrd || h.type == kTrap) {
+    const double big = std::fmax(h.ext[0], std::fmax(h.ext[1], h.ext[2]));
+    if (h.dz < kFineFeature * big) h.flags |= kFp64Only;
+    return;
+  }
+  const double big = std::fmax(h.ext[0], h.ext[2]);
+  for (int k = 0; k + 1 < h.nz; k++) {
+    if (h.z[k + 1] - h.z[k] < kFineFeature * big) h.flags |= kFp64Only;
+    if ((h.inner >> k) & 1u) {
+      for (int j = k; j <= k + 1; j++) {  // wall thickness at both planes of the section
+        const double ro = h.out[k].a * h.z[j] + h.out[k].b, ri = h.in[k].a * h.z[j] + h.in[k].b;
+        if (ri > 0 && ro - ri < kFineFeature * big) h.flags |= kFp64Only;
+      }
+    }
+  }
+}
+
 inline void init_desc(Desc& h, int type) {
   std::memset(&h, 0, sizeof(h));
   h.type = type;
@@ -99,6 +124,7 @@ inline Built build_box(double dx, double dy, double dz, Desc& h) {
   h.D[0] = dx; h.D[1] = dy; h.D[2] = dz;
   h.dz = dz;
   h.ext[0] = dx; h.ext[1] = dy; h.ext[2] = dz;
+  mark_fine_features(h);
   fill_f32(h);
   return built_ok();
 }
@@ -142,6 +168,7 @@ inline Built build_trap(const double p[11], int type, Desc& h) {
   h.dz = dz;
   for (int k = 0; k < 8; k++)
     for (int i = 0; i < 3; i++) h.ext[i] = std::fmax(h.ext[i], std::fabs(v[k][i]));
+  mark_fine_features(h);
   fill_f32(h);
   return built_ok();
 }
@@ -178,6 +205,7 @@ inline Built build_pcon(int type, int nz, const double* z, const double* rmin, c
   const double twopi = 6.283185307179586, pi = 3.141592653589793;
   if (dphi < twopi) h.flags |= kHasPhi;
   if (dphi > pi) h.flags |= kPhiWide;
+  if (dphi < twopi && (dphi < kFineFeature || twopi - dphi < kFineFeature)) h.flags |= kFp64Only;
   const double ephi = sphi + dphi;
   h.ns[0] = std::sin(sphi);
   h.ns[1] = -std::cos(sphi);
@@ -188,6 +216,7 @@ inline Built build_pcon(int type, int nz, const double* z, const double* rmin, c
   for (int k = 0; k < nz; k++) rm = std::fmax(rm, rmax[k]);
   h.ext[0] = h.ext[1] = rm;
   h.ext[2] = std::fmax(std::fabs(z[0]), std::fabs(z[nz - 1]));
+  mark_fine_features(h);
   fill_f32(h);
   return built_ok();
 }

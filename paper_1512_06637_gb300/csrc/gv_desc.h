@@ -31,7 +31,10 @@ constexpr double kTangent = 1e-12;
 constexpr double kMerge = 1e-12;
 constexpr double kDisc = 16 * 1.1102230246251565e-16;
 
-enum : int32_t { kHasPhi = 1, kPhiWide = 2 };
+// kFp64Only: the solid has a feature finer than 2^-16 of its size (a wall, a z-section, a phi
+// wedge or the sliver a phi segment leaves out), which the binary32 passes cannot order reliably
+// against its neighbours: every pass evaluates it in binary64 (as booleans).
+enum : int32_t { kHasPhi = 1, kPhiWide = 2, kFp64Only = 4 };
 
 struct Line {   // R(z) = a*z + b, k = 1 / sqrt(1 + a*a)
   double a, b, k;

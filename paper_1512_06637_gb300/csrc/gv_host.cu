@@ -253,6 +253,26 @@ gv_status gv_query(const gv_solid* s, const gv_tracks* t, gv_precision prec, con
   return GV_OK;
 }
 
+gv_status gv_debug_status(uint32_t* codes, int64_t* first_index, int32_t clear) {
+  if (!codes || !first_index) return set_error(GV_ERR_INVALID_ARG, "gv_debug_status: NULL output");
+#ifdef GV_DEBUG
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned long long w32[2] = {0ull, ~0ull}, w64[2] = {0ull, ~0ull};
+  if (e == cudaSuccess) e = debug_read_query32(w32, clear != 0);
+  if (e == cudaSuccess) e = debug_read_query64(w64, clear != 0);
+  if (e != cudaSuccess) return cuda_error(e, "gv_debug_status");
+  *codes = (uint32_t)(w32[0] | w64[0]);
+  const unsigned long long m = w32[1] < w64[1] ? w32[1] : w64[1];
+  *first_index = m == ~0ull ? -1 : (int64_t)m;
+  return GV_OK;
+#else
+  (void)clear;
+  *codes = 0;
+  *first_index = -1;
+  return set_error(GV_ERR_UNSUPPORTED, "gv_debug_status: built without GV_DEBUG");
+#endif
+}
+
 const char* gv_last_error(void) { return g_last_error.c_str(); }
 
 const char* gv_version(void) { return "gvgeo 0.1 (sm_103a)"; }

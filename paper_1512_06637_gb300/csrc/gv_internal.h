@@ -52,6 +52,12 @@ int table_size(const gv_solid* const* solids, int n);
 gv_status cuda_error(cudaError_t e, const char* where);
 int sm_count();
 
+#ifdef GV_DEBUG
+// The device-check words of the query passes' translation units (gv_debug.cuh).
+cudaError_t debug_read_query32(unsigned long long out[2], bool clear);
+cudaError_t debug_read_query64(unsigned long long out[2], bool clear);
+#endif
+
 // Launchers (async on `stream`); return cudaGetLastError() of the launch.
 cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_t stream);
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,

@@ -421,6 +421,10 @@ __device__ __forceinline__ void query32(const Desc& S, const f32::TrackF& T, uns
   R.code = 1;
   R.din = R.dout = R.sin = R.sout = 0.f;
   if (R.flag) return;
+  if (S.flags & kFp64Only) {  // features finer than binary32 resolves: binary64 only
+    R.flag = true;
+    return;
+  }
   // frame tracks: the bounds add the local coordinates' and direction's own errors
   if (S.type == kBox) f32::box32<true>(S, T, want, R);
   else if (S.type == kTrd || S.type == kTrap) planar32_call(S, T, want, R);

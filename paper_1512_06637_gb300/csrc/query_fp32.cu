@@ -8,6 +8,7 @@
 // Pass 2 (k_refine_fp64): the same binary64 evaluation as the plain FP64 pass,
 // over the worklist only; its length is read on the device, so the two launches
 // need no host round trip.
+#include "gv_debug.cuh"
 #include "gv_internal.h"
 #include "solid_fp32.cuh"
 #include "solid_fp64.cuh"
@@ -79,6 +80,13 @@ __global__ void __launch_bounds__(Shape32<FAMILY>::threads, Shape32<FAMILY>::blo
       const f32::TrackF T = f32::track_from_words<(FAMILY >= 2)>(
           stage[buf][0][tid], stage[buf][1][tid], stage[buf][2][tid], dirs ? stage[buf][3][tid] : zero,
           dirs ? stage[buf][4][tid] : zero, dirs ? stage[buf][5][tid] : zero, dirs);
+#ifdef GV_DEBUG
+      if (dirs) {
+        const uint2 bu = stage[buf][3][tid], bv = stage[buf][4][tid], bw = stage[buf][5][tid];
+        GV_DCHECK(dbg_unit(__hiloint2double(bu.y, bu.x), __hiloint2double(bv.y, bv.x), __hiloint2double(bw.y, bw.x)),
+                  kDbgDirection, i);
+      }
+#endif
       f32::R32 R;
       R.flag = T.bad;
       R.code = 1;
@@ -175,6 +183,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) k_query_walk(const Desc* __re
         if (j < (unsigned long long)a.n) {
           i = (int64_t)j;
           T = f32::load_track<true>(X, Y, Z, Ux, Uy, Uz, i, dirs);
+          GV_DCHECK(!dirs || dbg_unit(a.u[i], a.v[i], a.w[i]), kDbgDirection, i);
           R.flag = T.bad;
           R.code = 1;
           R.din = R.dout = R.sin = R.sout = 0.f;
@@ -211,11 +220,13 @@ __global__ void __launch_bounds__(256) k_refine_fp64(const Desc* __restrict__ de
                         (a.dout ? f64::kWantDout : 0u) | (a.sin ? f64::kWantSin : 0u) |
                         (a.sout ? f64::kWantSout : 0u);
   const int64_t nref = (int64_t)*counter;
+  GV_DCHECK(nref <= a.n, kDbgWorklist, nref);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // consecutive entries go to consecutive blocks: a short worklist is spread over every
   // SM instead of filling the first few blocks (each entry is a long binary64 chain)
   for (int64_t j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; j < nref; j += stride) {
     const int64_t i = worklist[j];
+    GV_DCHECK(i < a.n, kDbgIndex, i);
     f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
     if (want & (f64::kWantDin | f64::kWantDout)) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
     f64::Result R;
@@ -246,8 +257,9 @@ cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* w
   // counter[0]: worklist length; counter[1]: next track of the lane-refill dispenser
   cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess || a.n == 0) return e;
-  // boolean solids have no binary32 pass: evaluated in binary64 (nothing goes to the worklist)
-  if (s->h.type == kBool) return launch_query_fp64(s, a, stream);
+  // boolean solids have no binary32 pass, and solids with features finer than binary32 resolves
+  // are evaluated in binary64 too (nothing goes to the worklist)
+  if (s->h.type == kBool || (s->h.flags & kFp64Only)) return launch_query_fp64(s, a, stream);
   const int threads = 256;
   int64_t blocks = (a.n + threads - 1) / threads;
   const int sms = sm_count();
@@ -284,5 +296,9 @@ cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* w
   }
   return cudaGetLastError();
 }
+
+#ifdef GV_DEBUG
+cudaError_t debug_read_query32(unsigned long long out[2], bool clear) { return dbg_read(out, clear); }
+#endif
 
 }  // namespace gv

@@ -1,5 +1,6 @@
 // query_fp64.cu -- the plain binary64 query pass: one thread per track, the
 // solid descriptor staged in shared memory, grid-stride over the basket.
+#include "gv_debug.cuh"
 #include "gv_internal.h"
 #include "solid_fp64.cuh"
 
@@ -23,7 +24,10 @@ __global__ void __launch_bounds__(256) k_query_fp64(const Desc* __restrict__ des
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
-    if (want & (f64::kWantDin | f64::kWantDout)) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
+    if (want & (f64::kWantDin | f64::kWantDout)) {
+      T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i];
+      GV_DCHECK(dbg_unit(T.u, T.v, T.w), kDbgDirection, i);
+    }
     f64::Result R;
     if (FAMILY == 0) f64::box_query(S, T, want, R);
     else if (FAMILY == 1) f64::planar_query(S, T, want, R);
@@ -52,5 +56,9 @@ cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_
   }
   return cudaGetLastError();
 }
+
+#ifdef GV_DEBUG
+cudaError_t debug_read_query64(unsigned long long out[2], bool clear) { return dbg_read(out, clear); }
+#endif
 
 }  // namespace gv

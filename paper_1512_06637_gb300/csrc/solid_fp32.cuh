@@ -899,7 +899,10 @@ __device__ inline bool pcon_begin(const Desc& S, const TrackF& T, unsigned want,
   if (has_phi) {
     if (!wide) PH = iv_and(iv_half(pa.g, pa.E, nds, ends, true, u), iv_half(pb.g, pb.E, nde, ende, true, u));
     else X2 = iv_and(iv_half(pa.g, pa.E, nds, ends, false, u), iv_half(pb.g, pb.E, nde, ende, false, u));
-    if (!X2.empty && !(X2.lo.v < X2.hi.v)) X2 = iv_none();
+    if (!X2.empty && !(X2.lo.v < X2.hi.v)) {  // no wedge along the ray, unless too close to tell
+      if (!apart(X2.lo, X2.hi)) u = true;
+      X2 = iv_none();
+    }
   }
   W.iw = T.w != 0 ? __frcp_rn(T.w) : 0.f;
   W.rad = rad;
@@ -1001,7 +1004,10 @@ __device__ inline void pcon_step(const Desc& S, const TrackF& T, Walk& W) {
       const Quad qi = quad32<TUBE, FRAME>(ai, TUBE ? 0.f : S.ial[k], Li, T, W.rad, W.erad, W.A0, W.rh, W.rl);
       u |= qi.unsure;
       X1 = iv_region(qi, -Li.g, Li.E, u);
-      if (!X1.empty && !(X1.lo.v < X1.hi.v)) X1 = iv_none();
+      if (!X1.empty && !(X1.lo.v < X1.hi.v)) {  // no hole along the ray, unless too close to tell
+        if (!apart(X1.lo, X1.hi)) u = true;
+        X1 = iv_none();
+      }
     }
     const Iv& X2 = W.X2;
     const Iv C = iv_and(lat, slab);
