@@ -132,3 +132,84 @@ def test_nav_invalid_nodes_and_outside(gv):
         want = O.nav_step(tr["x"], tr["y"], tr["z"], tr["dx"], tr["dy"], tr["dz"], node)
         check_nav(got, want, "fp64" if precision == "fp64" else "fp32", precision)
         assert (got["step"][::3] == -1).all()
+
+
+def grazing_nested_tracks(geo, n, seed):
+    """Nested detector tracks that touch or run along surfaces of placed volumes, six kinds in
+    turn: (0) on a shell's outer wall, tangent to it; (1) inside a shell, tangent downstream to
+    its inner wall; (2) in the gap outside a shell, tangent downstream to its outer wall;
+    (3) in a face plane of a rotated cell, outside the face, running along the plane over it;
+    (4) inside a shell, touching an edge of a cell; (5) in the gap between two shells at the
+    height of their end planes z = +/-500, running horizontally over a shell's end face."""
+    g = np.random.default_rng(seed)
+    nodes = geo["nodes"]
+    cells = [i for i, nd in enumerate(nodes) if nd["solid"] == 1]
+    half = np.array([4.5, 4.5, 112.5])
+    P, D = [], []
+    for m in range(n):
+        kind = m % 6
+        k = int(g.integers(1, 9))
+        rmin, rmax = 10.0 + 19.0 * k, 28.0 + 19.0 * k
+        if kind in (0, 1, 2):
+            R = rmin if kind == 1 else rmax
+            ph = g.uniform(0, 2 * math.pi)
+            z = g.choice([-250.0, 0.0, 250.0]) + g.uniform(-5, 5)
+            w = g.uniform(-0.3, 0.3)
+            c = math.sqrt(1 - w * w)
+            sg = 1.0 if g.random() < 0.5 else -1.0
+            d = np.array([-sg * c * math.sin(ph), sg * c * math.cos(ph), w])
+            # back off along the ray: kind 1 stays inside the shell, kind 2 in the 1 mm gap
+            t0 = {0: 0.0, 1: g.uniform(0.5, 5.0), 2: g.uniform(0.2, 0.9) * math.sqrt(2 * R) / c}[kind]
+            P.append(np.array([R * math.cos(ph), R * math.sin(ph), z]) - t0 * d)
+            D.append(d)
+        elif kind in (3, 4):
+            nd = nodes[cells[int(g.integers(0, len(cells)))]]
+            Rm, t = np.asarray(nd["R"]), np.asarray(nd["t"])
+            i, j = g.choice(3, 2, replace=False)
+            kk = 3 - i - j
+            si, sj = g.choice([-1.0, 1.0], 2)
+            dl = np.zeros(3)
+            if kind == 3:
+                pl = g.uniform(-1, 1, 3) * (half - 0.5)
+                pl[i] = si * half[i]
+                pl[j] = sj * (half[j] + g.uniform(0.2, 2.0))
+                a = g.uniform(-1.2, 1.2)
+                dl[j], dl[kk] = -sj * math.cos(a), math.sin(a)
+            else:
+                E = np.zeros(3)
+                E[i], E[j], E[kk] = si * half[i], sj * half[j], g.uniform(-half[kk] + 1, half[kk] - 1)
+                beta = g.uniform(0.2, 1.3)
+                dl[i], dl[j] = -si * math.cos(beta), sj * math.sin(beta)
+                pl = E - g.uniform(0.2, 2.0) * dl
+            P.append(t + Rm @ pl)
+            D.append(Rm @ dl)
+        else:
+            ph = g.uniform(0, 2 * math.pi)
+            r = rmax + g.uniform(0.2, 0.8)
+            a = ph + math.pi + g.uniform(-0.8, 0.8)
+            P.append([r * math.cos(ph), r * math.sin(ph), 500.0 if g.random() < 0.5 else -500.0])
+            D.append([math.cos(a), math.sin(a), 0.0])
+    D = np.asarray(D)
+    D /= np.linalg.norm(D, axis=1, keepdims=True)
+    return W.soa(np.asarray(P), D)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_nav_grazing(gv, precision):
+    """Locate and the navigation step for rays that touch or run along the surfaces of placed
+    volumes (the grazing-ray readings applied in each volume's frame): nodes and `next` exact,
+    step and safety within the stated tolerances."""
+    import torch
+    geo = W.nested_geometry()
+    G = gv.Geometry(geo["solids"], geo["nodes"])
+    O = oracle.Geometry(geo["solids"], geo["nodes"])
+    n = 24_000
+    tr = grazing_nested_tracks(geo, n, seed=77)
+    dev = to_device(tr, torch)
+    node = O.locate(tr["x"], tr["y"], tr["z"])
+    assert np.array_equal(G.locate(dev).cpu().numpy(), node)
+    out = G.step(dev, torch.from_numpy(node).cuda(), precision=precision, workspace=gv.Workspace(n))
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    want = O.nav_step(tr["x"], tr["y"], tr["z"], tr["dx"], tr["dy"], tr["dz"], node)
+    check_nav(got, want, "fp64" if precision == "fp64" else "fp32", f"grazing-{precision}")
