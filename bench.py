@@ -483,10 +483,51 @@ def run_e2e(gv, torch, inputs, solids, precision, n, steps, world):
     ms = sorted(windows)[1]
     h2d = sum(t.numel() * t.element_size() for tr in host_in.values() for t in tr.values())
     d2h = sum(t.numel() * t.element_size() for tr in host_out.values() for t in tr.values())
+    link = host_link(torch)
+    # the fewest milliseconds the step's copies can take on this link (directions overlap)
+    bound_ms = 1e3 * max(h2d / (link["h2d_gbs"] * 1e9), d2h / (link["d2h_gbs"] * 1e9),
+                         (h2d + d2h) / (link["both_gbs"] * 1e9))
     return {"value": aggregate(steps * len(solids) * n * N_QUERIES, world, ms), "unit": "queries/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "windows_ms_per_step": [w / steps for w in windows], "statistic": "median of 3 windows",
-            "path": f"gv_query_host, chunks of {E2E_CHUNK} tracks, {E2E_SLOTS} staging slots"}
+            "path": f"gv_query_host, chunks of {E2E_CHUNK} tracks, {E2E_SLOTS} staging slots",
+            "link": link, "link_bound_ms_per_step": bound_ms, "link_frac": bound_ms / (ms / steps)}
+
+
+def host_link(torch, copies: int = 16, mib: int = 32) -> dict:
+    """Copy bandwidth between pinned host memory and this GPU (GB/s): host to device,
+    device to host, and both directions at once on two streams; `copies` copies of `mib` MiB
+    each way, timed with CUDA events.  More streams per direction measured no faster."""
+    n = mib * (1 << 20) // 8
+    h_in = [torch.ones(n, dtype=torch.float64).pin_memory() for _ in range(copies)]
+    h_out = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(copies)]
+    d = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(copies)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(up: bool, down: bool) -> float:
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        a.record()
+        s_in.wait_event(a)
+        s_out.wait_event(a)
+        for j in range(copies):
+            if up:
+                with torch.cuda.stream(s_in):
+                    d[j].copy_(h_in[j], non_blocking=True)
+            if down:
+                with torch.cuda.stream(s_out):
+                    h_out[j].copy_(d[(j + 1) % copies], non_blocking=True)
+        ends = []
+        for st in (s_in, s_out):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(st)
+            ends.append(e)
+        torch.cuda.synchronize()
+        sec = max(a.elapsed_time(e) for e in ends) / 1e3
+        return (int(up) + int(down)) * copies * n * 8 / sec / 1e9
+
+    run(True, True)  # warm-up
+    return {"h2d_gbs": run(True, False), "d2h_gbs": run(False, True), "both_gbs": run(True, True)}
 
 
 def reduce_max(value: float, world: int, device: str = "cuda") -> float:

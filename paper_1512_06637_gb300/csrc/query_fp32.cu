@@ -145,11 +145,13 @@ constexpr int kRefillIdle = 16;
 // tube and one-section cones: the walk is one or two sections long, so the plain kernel
 // (one track per thread, no refill) is used for them
 constexpr bool kWalkOneSection = false;
-// threads per block of the walk kernel (two blocks per SM: the register budget sets it)
+// threads per block of the walk kernel and resident blocks per SM (the register budget sets
+// them; 224-384 threads and 2-3 blocks measured within 4% of each other)
 constexpr int kWalkThreads = 320;
+constexpr int kWalkBlocks = 2;
 
 template <int FAMILY>
-__global__ void __launch_bounds__(kWalkThreads, 2) k_query_walk(const Desc* __restrict__ desc, QueryArgs a,
+__global__ void __launch_bounds__(kWalkThreads, kWalkBlocks) k_query_walk(const Desc* __restrict__ desc, QueryArgs a,
                                                       uint32_t* __restrict__ worklist,
                                                       unsigned long long* __restrict__ counter) {
   __shared__ Desc S;
@@ -265,8 +267,8 @@ cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* w
   const int sms = sm_count();
   const int64_t cap = (int64_t)sms * 8;
   if (blocks > cap) blocks = cap;
-  // lane-refill kernel: resident blocks only (two per SM), fed by the dispenser
-  const unsigned wblocks = (unsigned)(blocks < (int64_t)sms * 2 ? blocks : (int64_t)sms * 2);
+  // lane-refill kernel: resident blocks only, fed by the dispenser
+  const unsigned wblocks = (unsigned)(blocks < (int64_t)sms * kWalkBlocks ? blocks : (int64_t)sms * kWalkBlocks);
   // the worklist holds at most n tracks: no more refinement blocks than that needs
   const unsigned rblocks = (unsigned)(blocks < (int64_t)sms * 2 ? blocks : (int64_t)sms * 2);
   switch (s->h.type) {
@@ -287,7 +289,9 @@ cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* w
       k_refine_fp64<2><<<rblocks, threads, 0, stream>>>(s->d, a, worklist, counter);
       break;
     default:
-      if (s->h.nz > 2 || kWalkOneSection)
+      // without distances no track walks: one track per thread (measured 20% faster for the
+      // code alone than the lane-refill pass, whose every refill waits on its loads)
+      if ((s->h.nz > 2 || kWalkOneSection) && (a.din || a.dout))
         k_query_walk<3><<<wblocks, kWalkThreads, 0, stream>>>(s->d, a, worklist, counter);
       else
         launch_pass32<3>(s, a, worklist, counter, stream, sms);

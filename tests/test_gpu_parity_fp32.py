@@ -119,10 +119,18 @@ def test_fp32_empty_single_and_subsets(gv):
     want = oracle.Solid.from_spec(spec).query(**tr)
     dev = to_device(tr, torch)
     sp = gv.Solid.from_spec(spec)
+    full = to_host(gv.query(sp, dev, precision="fp32_refine", workspace=ws))
     for subset in (("inside",), ("dist_out",), ("safety_in", "safety_out"), ("dist_in", "inside")):
         out = gv.query(sp, dev, precision="fp32_refine", workspace=ws, want=subset)
         torch.cuda.synchronize()
-        compare(to_host(out), want, "fp32", f"subset{subset}")
+        got = to_host(out)
+        compare(got, want, "fp32", f"subset{subset}")
+        # subsets without distances take the one-track-per-thread pass, the others the
+        # lane-refill pass.  The code is decided exactly on both; the other values may come
+        # from either precision (a track flagged for its distance gets all its values from
+        # binary64), so they are held to the oracle above, not to each other.
+        if "inside" in subset:
+            assert np.array_equal(got["inside"], full["inside"]), subset
 
 
 def test_fp32_workspace_too_small(gv):
