@@ -35,21 +35,22 @@ import workloads as W  # noqa: E402
 
 N_QUERIES = 5
 BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 doubles out
-# DRAM bytes per track of each binary32 pass, from one ncu capture of the full-size step
-# (dram__bytes_read.sum + dram__bytes_write.sum, one pass); valid only while the kernel
-# sources hash to the value recorded with them, else the bench reports traffic = null.
+# DRAM bytes per track of each binary32 pass, from one ncu capture per pass at 2^22 tracks
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch; results still in L2 at the end of a
+# launch are not counted, at most 129 MB); valid only while the kernel sources hash to the value
+# recorded with them, else the bench reports traffic = null.
 DRAM_CAPTURE = {
-    "sources_sha256": "021ad82be26c546dcc2602f5e6a90387c680130b9553e7e3b35d8a352983dcec",
-    "bytes_per_track": {'box': 78.94, 'trd': 79.18, 'tube': 79.29, 'cone': 79.37, 'polycone': 80.19},
-    "profile": "profiles/query_fp32_dram_full.md",
+    "sources_sha256": "3a8b6dd2b469b9327dca42c4b2201a52029cf18b2691fdf0d4a85c5cb1dbe0c6",
+    "bytes_per_track": {'box': 71.95, 'trd': 72.56, 'tube': 73.28, 'cone': 73.67, 'polycone': 72.29},
+    "profile": "profiles/query_fp32_passes_4M_counters.md",
 }
 # Warp instructions per track of each binary32 pass (smsp__inst_executed.sum of one launch ÷
-# its tracks, from an ncu capture of the 2^21-track case; the counts do not depend on the
-# basket size), valid while the kernel sources hash to the recorded value.
+# its tracks, from the same captures; the counts do not depend on the basket size), valid while
+# the kernel sources hash to the recorded value.
 ISSUE_CAPTURE = {
-    "sources_sha256": "021ad82be26c546dcc2602f5e6a90387c680130b9553e7e3b35d8a352983dcec",
-    "warp_inst_per_track": {'box': 18.90, 'trd': 34.62, 'tube': 61.16, 'cone': 56.84, 'polycone': 116.34},
-    "profile": "profiles/query_fp32_issue_2M.md",
+    "sources_sha256": "3a8b6dd2b469b9327dca42c4b2201a52029cf18b2691fdf0d4a85c5cb1dbe0c6",
+    "warp_inst_per_track": {'box': 18.61, 'trd': 34.34, 'tube': 62.04, 'cone': 57.16, 'polycone': 116.11},
+    "profile": "profiles/query_fp32_passes_4M_counters.md",
 }
 KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
 E2E_CHUNK = 1 << 22  # tracks per host-streaming chunk (2^19-2^22 measured: larger is faster)
@@ -260,6 +261,11 @@ def cpu_baseline_sweep(max_exp: int = 16):
     return {"cores": threads, "rows": res}
 
 
+def tracks_label(n: int) -> str:
+    """2^k when n is a power of two, else the number."""
+    return f"2^{n.bit_length() - 1}" if n > 0 and n & (n - 1) == 0 else str(n)
+
+
 def kernel_sources_sha256() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -414,9 +420,11 @@ def run_ours(args):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if precision == "fp32_refine" else "f64", "data": "synthetic",
-        "config": {"workload": "precision form: box, trd, tube, cone, polycone; 2^24 tracks per solid; "
-                               "all five queries", "tracks_per_solid": n, "precision": precision,
-                   "l2": "inputs larger than L2 (4 GB per step)", "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"precision form: box, trd, tube, cone, polycone; {tracks_label(n)} tracks per "
+                               "solid; all five queries", "tracks_per_solid": n, "precision": precision,
+                   "l2": f"inputs {'larger' if 5 * n * 48 > 129e6 else 'smaller'} than L2 "
+                         f"({5 * n * 48 / 1e9:.2f} GB per step)",
+                   "parallelism": f"replicas x{world}"},
         "per_solid_ms": per_solid_ms,
         "roofline": roofline,
         "alu_peaks": alu,
