@@ -53,6 +53,15 @@ ISSUE_CAPTURE = {
     "profile": "profiles/query_fp32_passes_4M_counters.md",
 }
 KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
+# FP64-pipe warp instructions per track of the binary64 pass on the 2^20-track tube and cone
+# (sm__inst_executed_pipe_fp64.sum of one launch / its tracks), valid while the binary64 sources
+# hash to the recorded value.
+FP64_CAPTURE = {
+    "sources_sha256": "4dc69b6188c7b4141fbba10369746d1a1fd63c45e8a3de4129a55fe85b88655d",
+    "fp64_warp_inst_per_track": {'tube': 17.13, 'cone': 11.62},
+    "profile": "profiles/query_fp64_tube_cone_1M_pipe.md",
+}
+FP64_KERNEL_SOURCES = ("solid_fp64.cuh", "query_fp64.cu", "gv_desc.h")
 E2E_CHUNK = 1 << 22  # tracks per host-streaming chunk (2^19-2^22 measured: larger is faster)
 E2E_SLOTS = 3
 
@@ -74,8 +83,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, navigation and serving forms")
-    ap.add_argument("--form", default="all", choices=["all", "batched", "transport", "peaks"],
-                    help="batched / transport: only that form (for profiling), --warmup then --steps calls")
+    ap.add_argument("--form", default="all", choices=["all", "batched", "transport", "peaks", "fp64"],
+                    help="batched / transport / fp64 (the binary64 tube and cone): only that form (for "
+                         "profiling); peaks: the probe rates")
     return ap.parse_args()
 
 
@@ -266,10 +276,10 @@ def tracks_label(n: int) -> str:
     return f"2^{n.bit_length() - 1}" if n > 0 and n & (n - 1) == 0 else str(n)
 
 
-def kernel_sources_sha256() -> str:
+def kernel_sources_sha256(files=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_1512_06637_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -439,7 +449,7 @@ def run_ours(args):
         del dev, outs
         torch.cuda.empty_cache()
         line["box1024"] = bench_box1024(gv, torch)
-        line["fp64_tube_cone_2e20"] = bench_fp64_m2(gv, torch, peaks)
+        line["fp64_tube_cone_2e20"] = bench_fp64_m2(gv, torch, peaks, line.get("alu_peaks"))
         line["sweep_dist_out"] = bench_sweep(gv, torch)
         line["batched"] = bench_batched(gv, torch, max(3, args.steps), peaks)
         line["nav"] = bench_nav(gv, torch, max(3, args.steps))
@@ -641,19 +651,29 @@ def bench_box1024(gv, torch, reps=5000):
     return res
 
 
-def bench_fp64_m2(gv, torch, peaks, reps=20):
+def bench_fp64_m2(gv, torch, peaks, alu=None, reps=20):
     """Tube (5,20,30,0,270 deg) and cone (0,10,5,25,40,0,360 deg), 2^20 tracks each, plain
-    binary64, all five queries (the binary64 kernels alone, against the HBM roof)."""
+    binary64, all five queries (the binary64 kernels alone), against the HBM roof and, while the
+    binary64 sources match the recorded capture, against the FP64 pipe: the captured FP64-pipe
+    warp instructions per track x tracks / time, over the probe's binary64 multiply-add rate in
+    warp instructions (its per-SM rate / 32 lanes x SMs x clock)."""
     res = {}
     n = 1 << 20
+    fp64_ok = FP64_CAPTURE["sources_sha256"] == kernel_sources_sha256(FP64_KERNEL_SOURCES)
     for name, spec in (("tube", W.TUBE_M2), ("cone", W.CONE_M2)):
         dev = {k: torch.from_numpy(v).cuda() for k, v in W.tracks_for_solid(spec, n, seed=8).items()}
         s = gv.Solid.from_spec(spec)
         out = gv.alloc_results(n, "cuda")
         ms = _timed(torch, lambda: gv.query(s, dev, precision="fp64", out=out), reps)
         gbs = n * BYTES_PER_TRACK / (ms * 1e-3) / 1e9
-        res[name] = {"queries_per_s": n * N_QUERIES / (ms * 1e-3), "us": ms * 1e3, "hbm_gbs": gbs,
-                     "hbm_frac": gbs / peaks["hbm_gbs"]}
+        r = {"queries_per_s": n * N_QUERIES / (ms * 1e-3), "us": ms * 1e3, "hbm_gbs": gbs,
+             "hbm_frac": gbs / peaks["hbm_gbs"], "fp64_pipe_frac": None}
+        per_track = FP64_CAPTURE["fp64_warp_inst_per_track"].get(name)
+        if alu is not None and fp64_ok and per_track is not None:
+            peak = alu["fp64_fma"]["per_clk_per_sm"] / 32.0 * alu["sms"] * alu["sm_mhz"] * 1e6
+            r["fp64_pipe_frac"] = per_track * n / (ms * 1e-3) / peak
+            r["fp64_pipe_source"] = FP64_CAPTURE["profile"]
+        res[name] = r
     return res
 
 
@@ -960,6 +980,15 @@ def main():
         run_batched_only(args)
     elif args.form == "transport":
         run_transport_only(args)
+    elif args.form == "fp64":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import paper_1512_06637_gb300 as gv
+        from paper_1512_06637_gb300 import build
+        build.build()
+        alu = bench_alu_peaks(torch, torch.cuda.current_device())
+        res = bench_fp64_m2(gv, torch, load_peaks(), alu, reps=max(1, args.steps))
+        print(json.dumps({"form": "fp64", **res}), flush=True)
     elif args.form == "peaks":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
