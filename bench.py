@@ -57,11 +57,11 @@ KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
 # (sm__inst_executed_pipe_fp64.sum of one launch / its tracks), valid while the binary64 sources
 # hash to the recorded value.
 FP64_CAPTURE = {
-    "sources_sha256": "4dc69b6188c7b4141fbba10369746d1a1fd63c45e8a3de4129a55fe85b88655d",
-    "fp64_warp_inst_per_track": {'tube': 17.13, 'cone': 11.62},
+    "sources_sha256": "ad19c0855b6e67b54bce452f66dec059caf213976983273709f4e8e2c6d725a5",
+    "fp64_warp_inst_per_track": {'tube': 10.29, 'cone': 7.07},
     "profile": "profiles/query_fp64_tube_cone_1M_pipe.md",
 }
-FP64_KERNEL_SOURCES = ("solid_fp64.cuh", "query_fp64.cu", "gv_desc.h")
+FP64_KERNEL_SOURCES = ("solid_fp64.cuh", "query_fp64.cu", "gv_desc.h")  # and work_class.cuh (sort pass only)
 E2E_CHUNK = 1 << 22  # tracks per host-streaming chunk (2^19-2^22 measured: larger is faster)
 E2E_SLOTS = 3
 
@@ -340,7 +340,8 @@ def run_ours(args):
     dev = {name: {k: torch.from_numpy(v).cuda() for k, v in tr.items()} for name, tr in inputs.items()}
     solids = {name: gv.Solid.from_spec(spec) for name, spec in specs()}
     outs = {name: gv.alloc_results(n, "cuda") for name in solids}
-    ws = gv.Workspace(n) if precision == "fp32_refine" else None
+    # the workspace holds the refinement worklist and the binary64 pass's work-class order
+    ws = gv.Workspace(n)
     stream = torch.cuda.current_stream()
     names = list(solids)
     launches_per_query = 2 if precision == "fp32_refine" else 1
@@ -415,7 +416,7 @@ def run_ours(args):
     roofline["issue_frac"] = None if issue is None else issue["frac"]
 
     refined = None
-    if ws is not None:
+    if precision == "fp32_refine":
         refined = {}
         for name in names:
             gv.query(solids[name], dev[name], precision=precision, out=outs[name], workspace=ws, stream=stream)
@@ -660,11 +661,12 @@ def bench_fp64_m2(gv, torch, peaks, alu=None, reps=20):
     res = {}
     n = 1 << 20
     fp64_ok = FP64_CAPTURE["sources_sha256"] == kernel_sources_sha256(FP64_KERNEL_SOURCES)
+    ws = gv.Workspace(n)  # lets the pass order the basket by work class
     for name, spec in (("tube", W.TUBE_M2), ("cone", W.CONE_M2)):
         dev = {k: torch.from_numpy(v).cuda() for k, v in W.tracks_for_solid(spec, n, seed=8).items()}
         s = gv.Solid.from_spec(spec)
         out = gv.alloc_results(n, "cuda")
-        ms = _timed(torch, lambda: gv.query(s, dev, precision="fp64", out=out), reps)
+        ms = _timed(torch, lambda: gv.query(s, dev, precision="fp64", out=out, workspace=ws), reps)
         gbs = n * BYTES_PER_TRACK / (ms * 1e-3) / 1e9
         r = {"queries_per_s": n * N_QUERIES / (ms * 1e-3), "us": ms * 1e3, "hbm_gbs": gbs,
              "hbm_frac": gbs / peaks["hbm_gbs"], "fp64_pipe_frac": None}
