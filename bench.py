@@ -935,7 +935,8 @@ def bench_alu_peaks(torch, index: int, reps: int = 5):
 
 def run_batched_only(args):
     """The batched form alone (for profiling): launch shape 256 threads x 2 tracks, as many
-    CTAs as fit, W warm-up and K timed graph replays, FP32 + refinement."""
+    CTAs as fit, W warm-up and K timed graph replays, FP32 + refinement (--precision fp64:
+    binary64)."""
     import torch
     import paper_1512_06637_gb300 as gv
     work = W.batched()
@@ -944,11 +945,13 @@ def run_batched_only(args):
     b = gv.Batch([gv.Solid.from_spec(sp) for sp in work["solids"]], work["offset"], work["n"], work["solid"])
     b.set_config(256, 2, 0)
     out = gv.alloc_results(n, "cuda")
+    prec = "fp64" if args.precision == "fp64" else "fp32_refine"
     for _ in range(args.warmup):
-        b.run(dev, out)
-    ms = _timed(torch, lambda: b.run(dev, out), max(1, args.steps))
-    print(json.dumps({"form": "batched", "tracks": n, "ms": ms, "queries_per_s": n * N_QUERIES / (ms * 1e-3),
-                      "refined": b.refined()}), flush=True)
+        b.run(dev, out, precision=prec)
+    ms = _timed(torch, lambda: b.run(dev, out, precision=prec), max(1, args.steps))
+    print(json.dumps({"form": "batched", "precision": prec, "tracks": n, "ms": ms,
+                      "queries_per_s": n * N_QUERIES / (ms * 1e-3),
+                      "refined": b.refined() if prec == "fp32_refine" else None}), flush=True)
 
 
 def run_transport_only(args, n=1 << 17, kmax=64):

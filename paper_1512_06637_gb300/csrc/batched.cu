@@ -25,6 +25,7 @@
 #include "gv_internal.h"
 #include "solid_fp32.cuh"
 #include "solid_fp64.cuh"
+#include "work_class.cuh"
 
 namespace gv {
 
@@ -41,18 +42,41 @@ __device__ __forceinline__ void stage_any(Desc& dst, const Desc* __restrict__ sr
 }
 
 // Binary64: one persistent kernel over all tiles; a CTA takes a tile, stages its solid when
-// it changes and evaluates the tile's tracks one per thread.
+// it changes, orders the tile's tracks by work class (f32::track_class) in shared memory and
+// evaluates them one per thread in that order.  The FP64 pipe spends the same on a warp
+// instruction whatever its active lanes, so warps of one class run fewer instructions; the
+// per-track arithmetic, and so every output bit, is the same in any order.
+constexpr int kTileItemsMax = 16;  // tracks per thread of a tile (the batch configuration's limit)
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_batched(const Desc* __restrict__ solids, const Tile* __restrict__ tiles,
                                                      int ntiles, unsigned* __restrict__ next, QueryArgs a) {
+  constexpr uint32_t NC = f32::kClasses;
   __shared__ Desc S;
   __shared__ int s_tile;
+  __shared__ uint16_t ord[THREADS * kTileItemsMax];  // tile offsets in class order
+  __shared__ unsigned cnt[NC], cur[NC];
   int loaded = -1;
   const unsigned want = (a.inside ? 1u : 0u) | (a.din ? 2u : 0u) | (a.dout ? 4u : 0u) | (a.sin ? 8u : 0u) |
                         (a.sout ? 16u : 0u);
   const bool dirs = want & 6u;
+  const uint2 *X = reinterpret_cast<const uint2*>(a.x), *Y = reinterpret_cast<const uint2*>(a.y),
+              *Z = reinterpret_cast<const uint2*>(a.z), *Ux = reinterpret_cast<const uint2*>(a.u),
+              *Uy = reinterpret_cast<const uint2*>(a.v), *Uz = reinterpret_cast<const uint2*>(a.w);
+  auto cls_of = [&](int64_t i) -> uint32_t {
+    bool bad = false;  // a value outside the binary32 range only lands in some class
+    const float x = f32::trunc_hi(__ldg(X + i), bad), y = f32::trunc_hi(__ldg(Y + i), bad),
+                z = f32::trunc_hi(__ldg(Z + i), bad);
+    float u = 0.f, v = 0.f, w = 0.f;
+    if (dirs) {
+      u = f32::trunc_hi(__ldg(Ux + i), bad);
+      v = f32::trunc_hi(__ldg(Uy + i), bad);
+      w = f32::trunc_hi(__ldg(Uz + i), bad);
+    }
+    return f32::track_class(S, x, y, z, u, v, w, dirs);
+  };
   for (;;) {
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(next, 1u);
+    if (threadIdx.x < NC) cnt[threadIdx.x] = 0u;
     __syncthreads();
     const int t = s_tile;
     if (t >= ntiles) break;
@@ -63,8 +87,24 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_batched(const Desc* 
       __syncthreads();
     }
     const int type = S.type;
-    for (int j = threadIdx.x; j < tl.len; j += THREADS) {
-      const int64_t i = tl.start + j;
+    // a tile longer than the order array (never with a valid configuration) keeps index order
+    const bool order = tl.len <= THREADS * kTileItemsMax;
+    if (order) {
+      for (int j = threadIdx.x; j < tl.len; j += THREADS) atomicAdd(&cnt[cls_of(tl.start + j)], 1u);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (uint32_t q = 0; q < NC; q++) {
+          cur[q] = run;
+          run += cnt[q];
+        }
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < tl.len; j += THREADS) ord[atomicAdd(&cur[cls_of(tl.start + j)], 1u)] = (uint16_t)j;
+      __syncthreads();
+    }
+    for (int p = threadIdx.x; p < tl.len; p += THREADS) {
+      const int64_t i = tl.start + (order ? (int)ord[p] : p);
       f64::Track T{a.x[i], a.y[i], a.z[i], 0, 0, 0};
       if (dirs) { T.u = a.u[i]; T.v = a.v[i]; T.w = a.w[i]; }
       f64::Result R;

@@ -98,6 +98,31 @@ def test_batched_alone_equals_mix_and_shapes(gv, work):
             assert torch.equal(alone[k], ref[k][o:o + m]), (bi, k)
 
 
+def test_batched_fp64_ordered_tiles_same_bits(gv, work):
+    """The binary64 batched kernel evaluates each tile in work-class order: every basket's
+    results are the same bits as the single-solid binary64 pass in index order, under several
+    launch shapes (tiles of 128 to 2048 tracks)."""
+    import torch
+    b = make_batch(gv, work)
+    dev = to_device(work["tracks"], torch)
+    n = dev["x"].numel()
+    outs = []
+    for threads, items, ctas in ((128, 1, 1), (512, 4, 0), (256, 2, 2)):
+        b.set_config(threads, items, ctas)
+        out = gv.alloc_results(n, "cuda")
+        b.run(dev, out, precision="fp64")
+        torch.cuda.synchronize()
+        outs.append(out)
+    for bi in (0, 17, 1000, 4095):
+        o, m, sid = int(work["offset"][bi]), int(work["n"][bi]), int(work["solid"][bi])
+        sub = {k: v[o:o + m].contiguous() for k, v in dev.items()}
+        alone = gv.query(gv.Solid.from_spec(work["solids"][sid]), sub, precision="fp64")
+        torch.cuda.synchronize()
+        for out in outs:
+            for k in QUERIES:
+                assert torch.equal(alone[k], out[k][o:o + m]), (bi, k)
+
+
 def test_batched_autotune(gv, work, want):
     import torch
     b = make_batch(gv, work)
