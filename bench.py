@@ -40,7 +40,7 @@ BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 double
 # launch are not counted, at most 129 MB); valid only while the kernel sources hash to the value
 # recorded with them, else the bench reports traffic = null.
 DRAM_CAPTURE = {
-    "sources_sha256": "0d62485181863c2203d03537adc32a0cc7f6d280c104fa5e666aec5c467e4bc7",
+    "sources_sha256": "3a8b6dd2b469b9327dca42c4b2201a52029cf18b2691fdf0d4a85c5cb1dbe0c6",
     "bytes_per_track": {'box': 71.86, 'trd': 72.49, 'tube': 73.25, 'cone': 73.68, 'polycone': 72.36},
     "profile": "profiles/query_fp32_passes_4M_counters.md",
 }
@@ -48,7 +48,7 @@ DRAM_CAPTURE = {
 # its tracks, from the same captures; the counts do not depend on the basket size), valid while
 # the kernel sources hash to the recorded value.
 ISSUE_CAPTURE = {
-    "sources_sha256": "0d62485181863c2203d03537adc32a0cc7f6d280c104fa5e666aec5c467e4bc7",
+    "sources_sha256": "3a8b6dd2b469b9327dca42c4b2201a52029cf18b2691fdf0d4a85c5cb1dbe0c6",
     "warp_inst_per_track": {'box': 18.61, 'trd': 34.34, 'tube': 62.04, 'cone': 57.16, 'polycone': 116.11},
     "profile": "profiles/query_fp32_passes_4M_counters.md",
 }
@@ -57,11 +57,11 @@ KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
 # (sm__inst_executed_pipe_fp64.sum of one launch / its tracks), valid while the binary64 sources
 # hash to the recorded value.
 FP64_CAPTURE = {
-    "sources_sha256": "ad19c0855b6e67b54bce452f66dec059caf213976983273709f4e8e2c6d725a5",
-    "fp64_warp_inst_per_track": {'tube': 10.29, 'cone': 7.07},
+    "sources_sha256": "abebc41503aa477ad3e90870679b3b3cd8cf0f455f83c7d6775af7a6e27fc756",
+    "fp64_warp_inst_per_track": {'tube': 10.27, 'cone': 7.14},
     "profile": "profiles/query_fp64_tube_cone_1M_pipe.md",
 }
-FP64_KERNEL_SOURCES = ("solid_fp64.cuh", "query_fp64.cu", "gv_desc.h")  # and work_class.cuh (sort pass only)
+FP64_KERNEL_SOURCES = ("solid_fp64.cuh", "query_fp64.cu", "gv_desc.h", "work_class.cuh")
 E2E_CHUNK = 1 << 22  # tracks per host-streaming chunk (2^19-2^22 measured: larger is faster)
 E2E_SLOTS = 3
 
@@ -340,8 +340,7 @@ def run_ours(args):
     dev = {name: {k: torch.from_numpy(v).cuda() for k, v in tr.items()} for name, tr in inputs.items()}
     solids = {name: gv.Solid.from_spec(spec) for name, spec in specs()}
     outs = {name: gv.alloc_results(n, "cuda") for name in solids}
-    # the workspace holds the refinement worklist and the binary64 pass's work-class order
-    ws = gv.Workspace(n)
+    ws = gv.Workspace(n) if precision == "fp32_refine" else None
     stream = torch.cuda.current_stream()
     names = list(solids)
     launches_per_query = 2 if precision == "fp32_refine" else 1
@@ -661,12 +660,11 @@ def bench_fp64_m2(gv, torch, peaks, alu=None, reps=20):
     res = {}
     n = 1 << 20
     fp64_ok = FP64_CAPTURE["sources_sha256"] == kernel_sources_sha256(FP64_KERNEL_SOURCES)
-    ws = gv.Workspace(n)  # lets the pass order the basket by work class
     for name, spec in (("tube", W.TUBE_M2), ("cone", W.CONE_M2)):
         dev = {k: torch.from_numpy(v).cuda() for k, v in W.tracks_for_solid(spec, n, seed=8).items()}
         s = gv.Solid.from_spec(spec)
         out = gv.alloc_results(n, "cuda")
-        ms = _timed(torch, lambda: gv.query(s, dev, precision="fp64", out=out, workspace=ws), reps)
+        ms = _timed(torch, lambda: gv.query(s, dev, precision="fp64", out=out), reps)
         gbs = n * BYTES_PER_TRACK / (ms * 1e-3) / 1e9
         r = {"queries_per_s": n * N_QUERIES / (ms * 1e-3), "us": ms * 1e3, "hbm_gbs": gbs,
              "hbm_frac": gbs / peaks["hbm_gbs"], "fp64_pipe_frac": None}

@@ -128,11 +128,10 @@ typedef struct {
   double *dist_in, *dist_out, *safety_in, *safety_out;
 } gv_results;
 
-/* --- device scratch of the query passes ----------------------------------- */
+/* --- device scratch for the FP32 + refinement pass ---------------------- */
 
 /* Allocates (cudaMalloc, on the current device) scratch for baskets of up to
- * max_tracks tracks: the refinement worklist (4 bytes per track), the binary64
- * pass's work-class order (4 bytes per track) and a counter. */
+ * max_tracks tracks: the refinement worklist (4 bytes per track) and a counter. */
 gv_status gv_workspace_create(int64_t max_tracks, gv_workspace** out);
 void gv_workspace_destroy(gv_workspace* ws);
 /* Number of tracks the last GV_FP32_REFINE query on this workspace sent to the
@@ -142,11 +141,11 @@ gv_status gv_workspace_refined(gv_workspace* ws, void* stream, int64_t* n_refine
 /* --- the queries --------------------------------------------------------- */
 
 /* All requested queries for one basket against one solid (VecGeom section, the
- * three questions).  ws must hold >= tracks->n for GV_FP32_REFINE.  It may be NULL
- * for GV_FP64; given and large enough, a GV_FP64 pass over a basket of a primitive
- * solid of at least 65536 tracks first orders the tracks by work class in it
- * (results are the same bits either way; the pass runs faster).  Asynchronous on
- * `stream`. */
+ * three questions).  ws may be NULL for GV_FP64 and must hold >= tracks->n for
+ * GV_FP32_REFINE.  With GV_FP64, a basket of a primitive solid with at least 2048
+ * tracks per SM is evaluated in tiles ordered by work class (inside, outside, near
+ * a surface): the results are the same bits as in index order, the pass is faster.
+ * Asynchronous on `stream`. */
 gv_status gv_query(const gv_solid* s, const gv_tracks* tracks, gv_precision prec,
                    const gv_results* res, gv_workspace* ws, void* stream);
 
@@ -368,8 +367,8 @@ void gv_server_destroy(gv_server* s);
  * through its own pool, a serving loop that cannot take cudaMalloc's implicit
  * device synchronisation, a plug-in with no allocator.  (The paper has no
  * counterpart; this is an interface convenience of this library.)
- * Its scratch (refinement worklist, work-class order and counter) is a fixed device
- * array owned by the library: every GPU that loads the library holds 8 MiB for it until the
+ * Its scratch (refinement worklist and counter) is a fixed device array owned by
+ * the library: every GPU that loads the library holds 4 MiB for it until the
  * process exits.  At most 1048576 (2^20) tracks per call; larger baskets return
  * GV_ERR_INVALID_ARG.  The call allocates nothing (no cudaMalloc, no cudaFree).
  * All calls share the one array: the counter is cleared on `stream` at the start

@@ -190,14 +190,10 @@ gv_status gv_workspace_create(int64_t max_tracks, gv_workspace** out) {
   gv_workspace* w = new (std::nothrow) gv_workspace;
   if (!w) return set_error(GV_ERR_OUT_OF_MEMORY, "host allocation failed");
   w->idx = nullptr;
-  w->perm = nullptr;
   w->counter = nullptr;
   w->cap = max_tracks;
   cudaError_t e = cudaGetDevice(&w->device);
-  // the refinement worklist, then the binary64 pass's work-class order: max_tracks entries each
-  const size_t cap = (size_t)(max_tracks > 0 ? max_tracks : 1);
-  if (e == cudaSuccess) e = cudaMalloc(&w->idx, 2 * sizeof(uint32_t) * cap);
-  if (e == cudaSuccess) w->perm = w->idx + cap;
+  if (e == cudaSuccess) e = cudaMalloc(&w->idx, sizeof(uint32_t) * (size_t)(max_tracks > 0 ? max_tracks : 1));
   if (e == cudaSuccess) e = cudaMalloc(&w->counter, 64);
   if (e == cudaSuccess) e = cudaMemset(w->counter, 0, 64);
   if (e != cudaSuccess) {
@@ -247,12 +243,11 @@ gv_status gv_query(const gv_solid* s, const gv_tracks* t, gv_precision prec, con
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (prec == GV_FP64) {
-    // a workspace large enough for the basket lets the pass order the tracks by work class
-    e = launch_query_fp64(s, a, (ws && ws->cap >= t->n) ? ws->perm : nullptr, st);
+    e = launch_query_fp64(s, a, st);
   } else {
     if (!ws) return set_error(GV_ERR_INVALID_ARG, "GV_FP32_REFINE needs a workspace");
     if (ws->cap < t->n) return set_error(GV_ERR_OUT_OF_MEMORY, "workspace smaller than the basket");
-    e = launch_query_fp32(s, a, ws->idx, ws->counter, ws->perm, st);
+    e = launch_query_fp32(s, a, ws->idx, ws->counter, st);
   }
   if (e != cudaSuccess) return cuda_error(e, "gv_query launch");
   return GV_OK;

@@ -17,7 +17,6 @@ struct gv_solid {
 
 struct gv_workspace {
   uint32_t* idx;                 // refinement worklist, `cap` entries
-  uint32_t* perm;                // work-class order of a basket, `cap` entries (after idx)
   unsigned long long* counter;   // worklist length (device)
   int64_t cap;
   int device;
@@ -60,10 +59,8 @@ cudaError_t debug_read_query64(unsigned long long out[2], bool clear);
 #endif
 
 // Launchers (async on `stream`); return cudaGetLastError() of the launch.
-// perm: device scratch of a.n entries for the binary64 pass's work-class order, or null (no
-// ordering); worklist: scratch of a.n entries for the refinement worklist.
-cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, uint32_t* perm, cudaStream_t stream);
+cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_t stream);
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,
-                              unsigned long long* counter, uint32_t* perm, cudaStream_t stream);
+                              unsigned long long* counter, cudaStream_t stream);
 
 }  // namespace gv

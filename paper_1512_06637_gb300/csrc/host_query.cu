@@ -19,7 +19,6 @@ struct gv_pipeline {
     int8_t* code;
     double* res[4];        // dist_in dist_out safety_in safety_out
     uint32_t* idx;         // refinement worklist
-    uint32_t* perm;        // work-class order of the binary64 pass
     unsigned long long* counter;
     cudaEvent_t in_ready, comp_done, out_done;
     bool used;
@@ -78,7 +77,7 @@ gv_status gv_pipeline_create(int64_t chunk_tracks, int32_t slots, gv_pipeline** 
   p->next = 0;
   cudaError_t e = cudaGetDevice(&p->device);
   const size_t m = (size_t)chunk_tracks;
-  const size_t per_slot = 6 * align256(8 * m) + align256(m) + 4 * align256(8 * m) + 2 * align256(4 * m) + 256;
+  const size_t per_slot = 6 * align256(8 * m) + align256(m) + 4 * align256(8 * m) + align256(4 * m) + 256;
   if (e == cudaSuccess) e = cudaMalloc(&p->mem, per_slot * (size_t)slots);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_comp, cudaStreamNonBlocking);
@@ -92,7 +91,6 @@ gv_status gv_pipeline_create(int64_t chunk_tracks, int32_t slots, gv_pipeline** 
     S.code = reinterpret_cast<int8_t*>(base); base += align256(m);
     for (int j = 0; j < 4; j++) { S.res[j] = reinterpret_cast<double*>(base); base += align256(8 * m); }
     S.idx = reinterpret_cast<uint32_t*>(base); base += align256(4 * m);
-    S.perm = reinterpret_cast<uint32_t*>(base); base += align256(4 * m);
     S.counter = reinterpret_cast<unsigned long long*>(base);
     e = cudaEventCreateWithFlags(&S.in_ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.comp_done, cudaEventDisableTiming);
@@ -158,8 +156,7 @@ gv_status gv_query_host(const gv_solid* s, const gv_tracks* t, gv_precision prec
                   dirs ? S.in[5] : nullptr, res->inside ? S.code : nullptr,
                   hres[0] ? S.res[0] : nullptr, hres[1] ? S.res[1] : nullptr, hres[2] ? S.res[2] : nullptr,
                   hres[3] ? S.res[3] : nullptr, m};
-      e = prec == GV_FP64 ? launch_query_fp64(s, a, S.perm, p->s_comp)
-                          : launch_query_fp32(s, a, S.idx, S.counter, S.perm, p->s_comp);
+      e = prec == GV_FP64 ? launch_query_fp64(s, a, p->s_comp) : launch_query_fp32(s, a, S.idx, S.counter, p->s_comp);
     }
     if (e == cudaSuccess) e = cudaEventRecord(S.comp_done, p->s_comp);
     // copy out

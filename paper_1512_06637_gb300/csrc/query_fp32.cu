@@ -255,13 +255,13 @@ void launch_pass32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist, un
 }
 
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,
-                              unsigned long long* counter, uint32_t* perm, cudaStream_t stream) {
+                              unsigned long long* counter, cudaStream_t stream) {
   // counter[0]: worklist length; counter[1]: next track of the lane-refill dispenser
   cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess || a.n == 0) return e;
   // boolean solids have no binary32 pass, and solids with features finer than binary32 resolves
   // are evaluated in binary64 too (nothing goes to the worklist)
-  if (s->h.type == kBool || (s->h.flags & kFp64Only)) return launch_query_fp64(s, a, perm, stream);
+  if (s->h.type == kBool || (s->h.flags & kFp64Only)) return launch_query_fp64(s, a, stream);
   const int threads = 256;
   int64_t blocks = (a.n + threads - 1) / threads;
   const int sms = sm_count();

@@ -1,5 +1,5 @@
 // query_static.cu -- gv_query_fp32_static: the FP32 + refinement query pass with
-// its scratch (refinement worklist, class order and counter) in a fixed device array that
+// its scratch (refinement worklist and counter) in a fixed device array that
 // the library owns for the life of the process, so that the call itself never
 // allocates device memory.
 //
@@ -14,7 +14,7 @@
 //  - at most kStaticMaxTracks tracks per call (larger baskets are rejected
 //    with GV_ERR_INVALID_ARG before anything is enqueued);
 //  - the array is a static __device__ object: every GPU that loads the library
-//    holds it (8 MiB + 256 B) until the process exits;
+//    holds it (4 MiB + 256 B) until the process exits;
 //  - all calls share the one array; the counter is cleared (cudaMemsetAsync on
 //    the caller's stream) at the start of every call and the worklist keeps
 //    whatever the last call left in it.  Calls that overlap on the GPU (on
@@ -35,9 +35,7 @@ namespace gv {
 constexpr int64_t kStaticMaxTracks = int64_t(1) << 20;
 constexpr size_t kStaticCounterBytes = 256;  // counter, padded to keep the worklist aligned
 
-// counter, refinement worklist, work-class order of the binary64 pass (booleans and fine-featured
-// solids)
-static __device__ __align__(256) unsigned char g_static_scratch[kStaticCounterBytes + 2 * sizeof(uint32_t) * kStaticMaxTracks];
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticCounterBytes + sizeof(uint32_t) * kStaticMaxTracks];
 
 namespace {
 constexpr int kMaxDevices = 64;
@@ -92,8 +90,7 @@ extern "C" gv_status gv_query_fp32_static(const gv_solid* s, const gv_tracks* t,
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(base);
   uint32_t* worklist = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) + kStaticCounterBytes);
   // launch_query_fp32 clears the counter on the stream before the bulk pass
-  uint32_t* perm = worklist + kStaticMaxTracks;
-  const cudaError_t e = launch_query_fp32(s, a, worklist, counter, perm, (cudaStream_t)stream);
+  const cudaError_t e = launch_query_fp32(s, a, worklist, counter, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_error(e, "gv_query_fp32_static launch");
   return GV_OK;
 }

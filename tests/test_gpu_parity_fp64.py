@@ -171,23 +171,27 @@ def test_fp64_degenerate_solids(gv, i):
 @pytest.mark.gpu
 @pytest.mark.parametrize("kind", ["box", "trd", "trap", "tube", "cone", "polycone"])
 def test_fp64_class_order_same_bits(gv, kind):
-    """Given a workspace, the binary64 pass orders a basket of >= 65536 tracks by work class
-    before evaluating it; the per-track arithmetic is unchanged, so every output equals the
-    unordered pass bit for bit (ragged basket: several 4096-track tiles and a partial one), and a
+    """A basket large enough to give every SM a tile is evaluated in tiles ordered by work class;
+    the per-track arithmetic is unchanged, so every output equals the index-order pass (the same
+    tracks queried in small chunks) bit for bit (ragged basket: a partial last tile), and a
     sample is held to the oracle."""
     import torch
     spec = next(sp for sp in TABLE if sp["kind"] == "trap") if kind == "trap" else SPECS[kind]
-    n = (1 << 17) + 123
+    n = (1 << 19) + 123
     tr = W.tracks_for_solid(spec, n, seed=31)
     dev = to_device(tr, torch)
     s = gv.Solid.from_spec(spec)
-    plain = to_host(gv.query(s, dev, precision="fp64"))
-    ws = gv.Workspace(n)
-    ordered = to_host(gv.query(s, dev, precision="fp64", workspace=ws))
+    tiled = to_host(gv.query(s, dev, precision="fp64"))
+    chunk = 1 << 15
+    parts = []
+    for o in range(0, n, chunk):
+        sub = {k: v[o:o + chunk].contiguous() for k, v in dev.items()}
+        parts.append(to_host(gv.query(s, sub, precision="fp64")))
     torch.cuda.synchronize()
-    for k in plain:
-        assert np.array_equal(plain[k].view(np.uint8), ordered[k].view(np.uint8)), (kind, k)
-    idx = np.arange(0, n, 37)
+    for k in tiled:
+        plain = np.concatenate([p[k] for p in parts])
+        assert np.array_equal(plain.view(np.uint8), tiled[k].view(np.uint8)), (kind, k)
+    idx = np.arange(0, n, 97)
     sub = {k: v[idx] for k, v in tr.items()}
     want = oracle.Solid.from_spec(spec).query(**sub)
-    compare({k: v[idx] for k, v in ordered.items()}, want, "fp64", f"ordered-{kind}")
+    compare({k: v[idx] for k, v in tiled.items()}, want, "fp64", f"tiled-{kind}")
