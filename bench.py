@@ -57,7 +57,7 @@ KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
 # (sm__inst_executed_pipe_fp64.sum of one launch / its tracks), valid while the binary64 sources
 # hash to the recorded value.
 FP64_CAPTURE = {
-    "sources_sha256": "abebc41503aa477ad3e90870679b3b3cd8cf0f455f83c7d6775af7a6e27fc756",
+    "sources_sha256": "a562337b158d4b03530a2b9896ff0c944b34ed14b299e68df71c029812143863",
     "fp64_warp_inst_per_track": {'tube': 10.27, 'cone': 7.14},
     "profile": "profiles/query_fp64_tube_cone_1M_pipe.md",
 }

@@ -123,9 +123,15 @@ __global__ void __launch_bounds__(256) k_query_fp64_tiles(const Desc* __restrict
 
 template <int FAMILY>
 static int64_t tiles_grid(int64_t tiles, int sms) {
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_query_fp64_tiles<FAMILY>, 256, 0) != cudaSuccess || occ < 1)
-    occ = 1;
+  // resident blocks per SM of the kernel (queried once: it depends only on the kernel and the GPU)
+  static const int occ = [] {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_query_fp64_tiles<FAMILY>, 256, 0) != cudaSuccess || o < 1) {
+      cudaGetLastError();  // leave no error behind for the launch check
+      o = 1;
+    }
+    return o;
+  }();
   return tiles < (int64_t)sms * occ ? tiles : (int64_t)sms * occ;
 }
 
