@@ -195,3 +195,30 @@ def test_fp64_class_order_same_bits(gv, kind):
     sub = {k: v[idx] for k, v in tr.items()}
     want = oracle.Solid.from_spec(spec).query(**sub)
     compare({k: v[idx] for k, v in tiled.items()}, want, "fp64", f"tiled-{kind}")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["box", "polycone"])
+@pytest.mark.parametrize("want", [("inside", "safety_in", "safety_out"), ("dist_in",), ("inside", "dist_out")])
+def test_fp64_class_order_subsets(gv, kind, want):
+    """Subsets of the queries through the work-class tiles (no directions: the classes come from
+    the point alone) give the same bits as the index-order pass over small chunks."""
+    import torch
+    spec = SPECS[kind]
+    n = (1 << 19) + 7
+    tr = W.tracks_for_solid(spec, n, seed=41)
+    dev = to_device(tr, torch)
+    if "dist_in" not in want and "dist_out" not in want:
+        for k in ("dx", "dy", "dz"):
+            dev[k] = None
+    s = gv.Solid.from_spec(spec)
+    tiled = to_host(gv.query(s, dev, precision="fp64", want=want))
+    chunk = 1 << 15
+    parts = []
+    for o in range(0, n, chunk):
+        sub = {k: (None if v is None else v[o:o + chunk].contiguous()) for k, v in dev.items()}
+        parts.append(to_host(gv.query(s, sub, precision="fp64", want=want)))
+    torch.cuda.synchronize()
+    for k in want:
+        plain = np.concatenate([p[k] for p in parts])
+        assert np.array_equal(plain.view(np.uint8), tiled[k].view(np.uint8)), (kind, want, k)
