@@ -335,6 +335,42 @@ __global__ void __launch_bounds__(256) k_nav_fp64(const NodeD* __restrict__ node
   }
 }
 
+// The same in tiles of 256 * kNavTileItems tracks per block iteration: longer runs of one kind, so
+// fewer warps straddle two kinds.  Taken for baskets of at least four tiles per resident block
+// (two per SM), so that the last round of tiles leaves few SMs idle.
+constexpr int kNavTileItems = 4;
+__global__ void __launch_bounds__(256) k_nav_fp64_tiles(const NodeD* __restrict__ nodes,
+                                                        const int32_t* __restrict__ children,
+                                                        const Desc* __restrict__ solids, int nnodes, NavArgs a,
+                                                        Vox vox) {
+  constexpr int TILE = 256 * kNavTileItems;
+  __shared__ int scount[kKinds];
+  __shared__ uint16_t sperm[TILE];
+  __shared__ uint8_t skind[TILE];
+  const int t = threadIdx.x;
+  for (int64_t t0 = (int64_t)blockIdx.x * TILE; t0 < a.n; t0 += (int64_t)gridDim.x * TILE) {  // block-uniform
+    const int len = a.n - t0 < TILE ? (int)(a.n - t0) : TILE;
+    if (t < kKinds) scount[t] = 0;
+    __syncthreads();
+    for (int j = t; j < len; j += 256) {
+      const int32_t v = a.node[t0 + j];
+      const int kind = (v >= 0 && v < nnodes) ? volume_kind(nodes, solids, v, vox) : kKinds - 2;
+      skind[j] = (uint8_t)kind;
+      atomicAdd(&scount[kind], 1);
+    }
+    __syncthreads();
+    if (t == 0) {
+      int acc = 0;
+      for (int k = 0; k < kKinds; k++) { const int c = scount[k]; scount[k] = acc; acc += c; }
+    }
+    __syncthreads();
+    for (int j = t; j < len; j += 256) sperm[atomicAdd(&scount[skind[j]], 1)] = (uint16_t)j;
+    __syncthreads();
+    for (int r = t; r < len; r += 256) nav_step64(nodes, children, solids, nnodes, a, t0 + sperm[r], vox);
+    __syncthreads();  // the tile's shared arrays are reused by the next tile
+  }
+}
+
 __global__ void __launch_bounds__(256) k_nav_refine(const NodeD* __restrict__ nodes, const int32_t* __restrict__ children,
                                                     const Desc* __restrict__ solids, int nnodes, NavArgs a,
                                                     const uint32_t* __restrict__ wl,
@@ -1221,8 +1257,15 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
   cudaStream_t st = (cudaStream_t)stream;
   const int sms = sm_count();
   if (prec == GV_FP64) {
-    int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sms * 8);
-    k_nav_fp64<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, vox_of(g));
+    const int64_t tile = 256 * kNavTileItems;
+    if (t->n >= (int64_t)sms * 2 * 4 * tile) {
+      const int64_t blocks = std::min<int64_t>((t->n + tile - 1) / tile, (int64_t)sms * 2);
+      k_nav_fp64_tiles<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a,
+                                                         vox_of(g));
+    } else {
+      int64_t blocks = std::min<int64_t>((t->n + 255) / 256, (int64_t)sms * 8);
+      k_nav_fp64<<<(unsigned)blocks, 256, 0, st>>>(g->d_nodes, g->d_children, g->d_solids, g->nnodes, a, vox_of(g));
+    }
   } else {
     if (!ws) return set_error(GV_ERR_INVALID_ARG, "nav: GV_FP32_REFINE needs a workspace");
     if (ws->cap < t->n) return set_error(GV_ERR_OUT_OF_MEMORY, "nav: workspace smaller than the basket");

@@ -213,3 +213,31 @@ def test_nav_grazing(gv, precision):
     got = {k: v.cpu().numpy() for k, v in out.items()}
     want = O.nav_step(tr["x"], tr["y"], tr["z"], tr["dx"], tr["dy"], tr["dz"], node)
     check_nav(got, want, "fp64" if precision == "fp64" else "fp32", f"grazing-{precision}")
+
+
+def test_nav_fp64_tiles_same_bits(gv):
+    """Baskets of at least eight 1024-track tiles per SM take the tiled binary64 step (longer runs
+    of one volume kind); the per-track arithmetic is unchanged, so step, safety and next equal
+    the 256-track-block pass over small chunks bit for bit, in both geometries."""
+    import torch
+    for name, geo in geoms():
+        G = gv.Geometry(geo["solids"], geo["nodes"])
+        O = oracle.Geometry(geo["solids"], geo["nodes"])
+        n = (1 << 21) + (1 << 20) + 11
+        tr = tracks_for(geo, n, seed=61)
+        dev = to_device(tr, torch)
+        node = G.locate(dev)
+        tiled = {k: v.cpu().numpy() for k, v in G.step(dev, node, precision="fp64").items()}
+        chunk = 1 << 16
+        parts = []
+        for o in range(0, n, chunk):
+            sub = {k: v[o:o + chunk].contiguous() for k, v in dev.items()}
+            parts.append({k: v.cpu().numpy() for k, v in G.step(sub, node[o:o + chunk].contiguous(), precision="fp64").items()})
+        torch.cuda.synchronize()
+        for k in tiled:
+            plain = np.concatenate([p[k] for p in parts])
+            assert np.array_equal(plain.view(np.uint8), tiled[k].view(np.uint8)), (name, k)
+        idx = np.arange(0, n, 211)
+        sub = {k: v[idx] for k, v in tr.items()}
+        want = O.nav_step(sub["x"], sub["y"], sub["z"], sub["dx"], sub["dy"], sub["dz"], node.cpu().numpy()[idx])
+        check_nav({k: v[idx] for k, v in tiled.items()}, want, "fp64", f"tiles-{name}")
