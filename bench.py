@@ -57,8 +57,8 @@ KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")
 # (sm__inst_executed_pipe_fp64.sum of one launch / its tracks), valid while the binary64 sources
 # hash to the recorded value.
 FP64_CAPTURE = {
-    "sources_sha256": "a562337b158d4b03530a2b9896ff0c944b34ed14b299e68df71c029812143863",
-    "fp64_warp_inst_per_track": {'tube': 10.27, 'cone': 7.14},
+    "sources_sha256": "a07399a0b4f95abb2a949a3ac5e9237dcdb23b0aab450eaf2b66597fbf4d00c7",
+    "fp64_warp_inst_per_track": {'tube': 10.47, 'cone': 7.29},
     "profile": "profiles/query_fp64_tube_cone_1M_pipe.md",
 }
 FP64_KERNEL_SOURCES = ("solid_fp64.cuh", "query_fp64.cu", "gv_desc.h", "work_class.cuh")

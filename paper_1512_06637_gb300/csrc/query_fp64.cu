@@ -1,6 +1,6 @@
 // query_fp64.cu -- the plain binary64 query pass: one thread per track, the solid
 // descriptor staged in shared memory.  A basket of a primitive solid large enough to give every
-// SM a tile is evaluated in tiles ordered by work class (k_query_fp64_tiles): the pass is bound
+// SM a 2048-track tile is evaluated in tiles ordered by work class (k_query_fp64_tiles): the pass is bound
 // by the FP64 pipe, which spends the same on a warp instruction whatever its active lanes, so
 // warps of one class (inside, outside and entering, outside and missing, near a surface) run
 // fewer instructions for the same tracks.  Smaller baskets and booleans go in index order,
@@ -47,14 +47,13 @@ __global__ void __launch_bounds__(256) k_query_fp64(const Desc* __restrict__ des
   }
 }
 
-// The binary64 pass in tiles ordered by work class: a block takes a tile of 256 * kTileItems64
+// The binary64 pass in tiles ordered by work class: a block takes a tile of 256 * ITEMS
 // consecutive tracks, classifies them (f32::track_class, from the high parts; the reads bring the
 // tile into the caches), orders the tile's offsets by class in shared memory (a count, a scan
 // and a scatter) and evaluates them in that order.
-constexpr int kTileItems64 = 8;
-template <int FAMILY>
+template <int FAMILY, int ITEMS>
 __global__ void __launch_bounds__(256) k_query_fp64_tiles(const Desc* __restrict__ desc, QueryArgs a) {
-  constexpr int NT = 256, TILE = NT * kTileItems64;
+  constexpr int NT = 256, TILE = NT * ITEMS;
   constexpr uint32_t NC = f32::kClasses;
   __shared__ Desc S;
   __shared__ uint16_t ord[TILE];
@@ -121,12 +120,12 @@ __global__ void __launch_bounds__(256) k_query_fp64_tiles(const Desc* __restrict
   }
 }
 
-template <int FAMILY>
+template <int FAMILY, int ITEMS>
 static int64_t tiles_grid(int64_t tiles, int sms) {
   // resident blocks per SM of the kernel (queried once: it depends only on the kernel and the GPU)
   static const int occ = [] {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_query_fp64_tiles<FAMILY>, 256, 0) != cudaSuccess || o < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_query_fp64_tiles<FAMILY, ITEMS>, 256, 0) != cudaSuccess || o < 1) {
       cudaGetLastError();  // leave no error behind for the launch check
       o = 1;
     }
@@ -139,14 +138,25 @@ cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_
   if (a.n == 0) return cudaSuccess;
   const int threads = 256;
   const int sms = sm_count();
-  const int64_t tile = 256 * kTileItems64;
-  if (s->h.type != kBool && a.n >= (int64_t)sms * tile) {  // a tile for every SM at least
-    const int64_t tiles = (a.n + tile - 1) / tile;
+  // tiles of 2048 tracks when the basket gives four of them to every resident block (two per SM),
+  // else of 1024 (more tiles, fewer SMs idle in the last round); none below one 2048 tile per SM
+  if (s->h.type != kBool && a.n >= (int64_t)sms * 2048) {
+    const bool big = a.n >= (int64_t)sms * 2 * 4 * 2048;
+    const int64_t tiles = big ? (a.n + 2047) / 2048 : (a.n + 1023) / 1024;
     switch (s->h.type) {
-      case kBox: k_query_fp64_tiles<0><<<(unsigned)tiles_grid<0>(tiles, sms), 256, 0, stream>>>(s->d, a); break;
+      case kBox:
+        if (big) k_query_fp64_tiles<0, 8><<<(unsigned)tiles_grid<0, 8>(tiles, sms), 256, 0, stream>>>(s->d, a);
+        else k_query_fp64_tiles<0, 4><<<(unsigned)tiles_grid<0, 4>(tiles, sms), 256, 0, stream>>>(s->d, a);
+        break;
       case kTrd:
-      case kTrap: k_query_fp64_tiles<1><<<(unsigned)tiles_grid<1>(tiles, sms), 256, 0, stream>>>(s->d, a); break;
-      default: k_query_fp64_tiles<2><<<(unsigned)tiles_grid<2>(tiles, sms), 256, 0, stream>>>(s->d, a); break;
+      case kTrap:
+        if (big) k_query_fp64_tiles<1, 8><<<(unsigned)tiles_grid<1, 8>(tiles, sms), 256, 0, stream>>>(s->d, a);
+        else k_query_fp64_tiles<1, 4><<<(unsigned)tiles_grid<1, 4>(tiles, sms), 256, 0, stream>>>(s->d, a);
+        break;
+      default:
+        if (big) k_query_fp64_tiles<2, 8><<<(unsigned)tiles_grid<2, 8>(tiles, sms), 256, 0, stream>>>(s->d, a);
+        else k_query_fp64_tiles<2, 4><<<(unsigned)tiles_grid<2, 4>(tiles, sms), 256, 0, stream>>>(s->d, a);
+        break;
     }
     return cudaGetLastError();
   }

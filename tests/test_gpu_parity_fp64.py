@@ -222,3 +222,26 @@ def test_fp64_class_order_subsets(gv, kind, want):
     for k in want:
         plain = np.concatenate([p[k] for p in parts])
         assert np.array_equal(plain.view(np.uint8), tiled[k].view(np.uint8)), (kind, want, k)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["box", "polycone"])
+def test_fp64_class_order_large_tiles(gv, kind):
+    """Baskets large enough for the 2048-track tiles (four per resident block) give the same bits
+    as the index-order pass over small chunks."""
+    import torch
+    spec = SPECS[kind]
+    n = (1 << 21) + (1 << 19) + 5
+    tr = W.tracks_for_solid(spec, n, seed=43)
+    dev = to_device(tr, torch)
+    s = gv.Solid.from_spec(spec)
+    tiled = to_host(gv.query(s, dev, precision="fp64"))
+    chunk = 1 << 16
+    parts = []
+    for o in range(0, n, chunk):
+        sub = {k: v[o:o + chunk].contiguous() for k, v in dev.items()}
+        parts.append(to_host(gv.query(s, sub, precision="fp64")))
+    torch.cuda.synchronize()
+    for k in tiled:
+        plain = np.concatenate([p[k] for p in parts])
+        assert np.array_equal(plain.view(np.uint8), tiled[k].view(np.uint8)), (kind, k)
