@@ -445,6 +445,8 @@ def run_ours(args):
     if refined is not None:
         line["refined_fraction"] = refined
     if not args.no_extra:
+        if precision == "fp32_refine":
+            line["fp64_form"] = bench_fp64_form(gv, torch, solids, dev, outs, names, n)
         # release the precision-form buffers before the other forms
         del dev, outs
         torch.cuda.empty_cache()
@@ -649,6 +651,17 @@ def bench_box1024(gv, torch, reps=5000):
             gv.query(s, dev, precision="fp32_refine", out=out, workspace=ws, stream=stream)
     res["fp32_refine_graph_us_per_call"] = 1e3 * _timed(torch, g.replay, reps)
     return res
+
+
+def bench_fp64_form(gv, torch, solids, dev, outs, names, n, reps=2):
+    """The same workload in plain binary64 (all five queries, the inputs already on the device):
+    per-solid CUDA-event times and the step's rate.  Baskets this large are evaluated in tiles
+    ordered by work class."""
+    per = {}
+    for name in names:
+        per[name] = _timed(torch, lambda: gv.query(solids[name], dev[name], precision="fp64", out=outs[name]), reps)
+    ms = sum(per.values())
+    return {"ms_per_step": ms, "queries_per_s": len(names) * n * N_QUERIES / (ms * 1e-3), "per_solid_ms": per}
 
 
 def bench_fp64_m2(gv, torch, peaks, alu=None, reps=20):
