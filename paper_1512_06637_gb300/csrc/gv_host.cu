@@ -192,6 +192,7 @@ gv_status gv_workspace_create(int64_t max_tracks, gv_workspace** out) {
   w->idx = nullptr;
   w->counter = nullptr;
   w->cap = max_tracks;
+  w->fused_blocks = 0;
   cudaError_t e = cudaGetDevice(&w->device);
   if (e == cudaSuccess) e = cudaMalloc(&w->idx, sizeof(uint32_t) * (size_t)(max_tracks > 0 ? max_tracks : 1));
   if (e == cudaSuccess) e = cudaMalloc(&w->counter, 64);
@@ -216,9 +217,21 @@ void gv_workspace_destroy(gv_workspace* w) {
 
 gv_status gv_workspace_refined(gv_workspace* w, void* stream, int64_t* n_refined) {
   if (!w || !n_refined) return set_error(GV_ERR_INVALID_ARG, "NULL workspace or output");
-  unsigned long long h = 0;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(&h, w->counter, sizeof(h), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaSuccess;
+  if (w->fused_blocks > 0) {  // the one-launch pass left one count per block
+    uint32_t h[16];
+    const int nb = w->fused_blocks < 16 ? w->fused_blocks : 16;
+    e = cudaMemcpyAsync(h, w->idx, sizeof(uint32_t) * (size_t)nb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "gv_workspace_refined");
+    int64_t sum = 0;
+    for (int b = 0; b < nb; b++) sum += h[b];
+    *n_refined = sum;
+    return GV_OK;
+  }
+  unsigned long long h = 0;
+  e = cudaMemcpyAsync(&h, w->counter, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "gv_workspace_refined");
   *n_refined = (int64_t)h;
@@ -247,7 +260,7 @@ gv_status gv_query(const gv_solid* s, const gv_tracks* t, gv_precision prec, con
   } else {
     if (!ws) return set_error(GV_ERR_INVALID_ARG, "GV_FP32_REFINE needs a workspace");
     if (ws->cap < t->n) return set_error(GV_ERR_OUT_OF_MEMORY, "workspace smaller than the basket");
-    e = launch_query_fp32(s, a, ws->idx, ws->counter, st);
+    e = launch_query_fp32(s, a, ws->idx, ws->counter, st, &ws->fused_blocks);
   }
   if (e != cudaSuccess) return cuda_error(e, "gv_query launch");
   return GV_OK;

@@ -20,6 +20,7 @@ struct gv_workspace {
   unsigned long long* counter;   // worklist length (device)
   int64_t cap;
   int device;
+  int fused_blocks;              // last query: blocks of the one-launch small-basket pass (0: none)
 };
 
 namespace gv {
@@ -60,7 +61,10 @@ cudaError_t debug_read_query64(unsigned long long out[2], bool clear);
 
 // Launchers (async on `stream`); return cudaGetLastError() of the launch.
 cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_t stream);
+// Baskets of at most 4096 tracks of a primitive solid take one launch that evaluates uncertain
+// tracks in binary64 on the spot; it writes each block's count of such tracks to worklist[block]
+// (not the counter) and reports its number of blocks in *fused_blocks (0: the two-pass path).
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,
-                              unsigned long long* counter, cudaStream_t stream);
+                              unsigned long long* counter, cudaStream_t stream, int* fused_blocks = nullptr);
 
 }  // namespace gv

@@ -1269,6 +1269,7 @@ gv_status gv_nav_step(const gv_geom* g, const gv_tracks* t, const int32_t* node,
   } else {
     if (!ws) return set_error(GV_ERR_INVALID_ARG, "nav: GV_FP32_REFINE needs a workspace");
     if (ws->cap < t->n) return set_error(GV_ERR_OUT_OF_MEMORY, "nav: workspace smaller than the basket");
+    ws->fused_blocks = 0;  // this pass counts its refinements in the counter
     cudaError_t e = cudaMemsetAsync(ws->counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_error(e, "nav: counter reset");
     const int64_t per_block = 256 / kLanes;

@@ -175,3 +175,32 @@ def test_fp32_degenerate_solids(gv, i):
     tr = W.tracks_for_solid(spec, 20011, seed=800 + i)
     got, refined = run32(gv, spec, tr)
     compare(got, oracle.Solid.from_spec(spec).query(**tr), "fp32", f"degenerate {spec['kind']}#{i}")
+
+
+@pytest.mark.parametrize("kind", ["box", "trd", "trap", "tube", "cone", "polycone"])
+def test_fp32_small_basket_one_launch_same_bits(gv, kind):
+    """Baskets of at most 4096 tracks take one launch that evaluates uncertain tracks in binary64
+    on the spot: the results equal those of the two-pass form (the same tracks inside a larger
+    basket) bit for bit, and the workspace reports as many tracks evaluated in binary64 as the
+    two-pass form sends to its refinement (the same tracks twice over: exactly twice as many)."""
+    import torch
+    spec = next(sp for sp in W.solid_table(24, seed=11) if sp["kind"] == "trap") if kind == "trap" else SPECS[kind]
+    # 30% of the points within 1e-9 of a surface, across the edge of the 5e-10 surface band:
+    # some of them the binary32 pass cannot decide
+    big = W.tracks_for_solid(spec, 1 << 17, seed=53, near_frac=0.3, band=1e-9)
+    dev = to_device(big, torch)
+    s = gv.Solid.from_spec(spec)
+    ws = gv.Workspace(1 << 17)
+    full = to_host(gv.query(s, dev, precision="fp32_refine", workspace=ws))
+    for m in (1, 37, 4096):
+        sub = {k: v[:m].contiguous() for k, v in dev.items()}
+        small = to_host(gv.query(s, sub, precision="fp32_refine", workspace=ws))
+        r1 = ws.refined()
+        torch.cuda.synchronize()
+        for k in small:
+            assert np.array_equal(small[k].view(np.uint8), full[k][:m].view(np.uint8)), (kind, m, k)
+        twice = {k: torch.cat([v, v]).contiguous() for k, v in sub.items()}
+        gv.query(s, twice, precision="fp32_refine", workspace=ws)
+        assert ws.refined() == 2 * r1, (kind, m)
+        if m == 4096:
+            assert r1 > 0, kind
