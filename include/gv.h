@@ -142,7 +142,7 @@ gv_status gv_workspace_refined(gv_workspace* ws, void* stream, int64_t* n_refine
 
 /* All requested queries for one basket against one solid (VecGeom section, the
  * three questions).  ws may be NULL for GV_FP64 and must hold >= tracks->n for
- * GV_FP32_REFINE.  With GV_FP32_REFINE, a basket of at most 4096 tracks of a
+ * GV_FP32_REFINE.  With GV_FP32_REFINE, a basket of at most 65536 tracks of a
  * primitive solid is one launch (uncertain tracks are evaluated in binary64 at
  * once, with the same bits as the refinement pass).  With GV_FP64, a basket of a primitive solid with at least 2048
  * tracks per SM is evaluated in tiles ordered by work class (inside, outside, near

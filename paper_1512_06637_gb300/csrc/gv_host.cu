@@ -220,8 +220,8 @@ gv_status gv_workspace_refined(gv_workspace* w, void* stream, int64_t* n_refined
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   if (w->fused_blocks > 0) {  // the one-launch pass left one count per block
-    uint32_t h[16];
-    const int nb = w->fused_blocks < 16 ? w->fused_blocks : 16;
+    uint32_t h[256];
+    const int nb = w->fused_blocks < 256 ? w->fused_blocks : 256;
     e = cudaMemcpyAsync(h, w->idx, sizeof(uint32_t) * (size_t)nb, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_error(e, "gv_workspace_refined");

@@ -61,7 +61,7 @@ cudaError_t debug_read_query64(unsigned long long out[2], bool clear);
 
 // Launchers (async on `stream`); return cudaGetLastError() of the launch.
 cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_t stream);
-// Baskets of at most 4096 tracks of a primitive solid take one launch that evaluates uncertain
+// Baskets of at most 65536 tracks of a primitive solid take one launch that evaluates uncertain
 // tracks in binary64 on the spot; it writes each block's count of such tracks to worklist[block]
 // (not the counter) and reports its number of blocks in *fused_blocks (0: the two-pass path).
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,

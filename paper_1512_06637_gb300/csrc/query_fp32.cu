@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(Shape32<FAMILY>::threads, Shape32<FAMILY>::blo
 // the same bits) instead of appending it to a worklist; each block writes how many tracks it
 // evaluated in binary64 to slots[blockIdx.x].  A call is then one launch with no counter reset:
 // for a basket this small the launches, not the tracks, set the time.
-constexpr int64_t kFusedMax = 4096;
+constexpr int64_t kFusedMax = 65536;
 template <int FAMILY>
 __global__ void __launch_bounds__(256) k_query_fused(const Desc* __restrict__ desc, QueryArgs a,
                                                      uint32_t* __restrict__ slots) {

@@ -179,7 +179,7 @@ def test_fp32_degenerate_solids(gv, i):
 
 @pytest.mark.parametrize("kind", ["box", "trd", "trap", "tube", "cone", "polycone"])
 def test_fp32_small_basket_one_launch_same_bits(gv, kind):
-    """Baskets of at most 4096 tracks take one launch that evaluates uncertain tracks in binary64
+    """Baskets of at most 65536 tracks take one launch that evaluates uncertain tracks in binary64
     on the spot: the results equal those of the two-pass form (the same tracks inside a larger
     basket) bit for bit, and the workspace reports as many tracks evaluated in binary64 as the
     two-pass form sends to its refinement (the same tracks twice over: exactly twice as many)."""
@@ -192,7 +192,7 @@ def test_fp32_small_basket_one_launch_same_bits(gv, kind):
     s = gv.Solid.from_spec(spec)
     ws = gv.Workspace(1 << 17)
     full = to_host(gv.query(s, dev, precision="fp32_refine", workspace=ws))
-    for m in (1, 37, 4096):
+    for m in (1, 37, 4096, 40000, 65536):
         sub = {k: v[:m].contiguous() for k, v in dev.items()}
         small = to_host(gv.query(s, sub, precision="fp32_refine", workspace=ws))
         r1 = ws.refined()
