@@ -40,16 +40,16 @@ BYTES_PER_TRACK = 6 * 8 + 1 + 4 * 8  # SoA point + direction in, code + 4 double
 # launch are not counted, at most 129 MB); valid only while the kernel sources hash to the value
 # recorded with them, else the bench reports traffic = null.
 DRAM_CAPTURE = {
-    "sources_sha256": "67d84ced8bae15aa6417a1ba120c5f66208d1f0123c6319af1016067a19ac5de",
-    "bytes_per_track": {'box': 71.82, 'trd': 72.45, 'tube': 73.30, 'cone': 73.63, 'polycone': 72.27},
+    "sources_sha256": "76e9d0d63b2268d4487bf17bc51db7e11e496f00247adc8c5ffbb5284f2e4c3a",
+    "bytes_per_track": {'box': 71.89, 'trd': 72.45, 'tube': 73.43, 'cone': 73.60, 'polycone': 72.30},
     "profile": "profiles/query_fp32_passes_4M_counters.md",
 }
 # Warp instructions per track of each binary32 pass (smsp__inst_executed.sum of one launch ÷
 # its tracks, from the same captures; the counts do not depend on the basket size), valid while
 # the kernel sources hash to the recorded value.
 ISSUE_CAPTURE = {
-    "sources_sha256": "67d84ced8bae15aa6417a1ba120c5f66208d1f0123c6319af1016067a19ac5de",
-    "warp_inst_per_track": {'box': 18.61, 'trd': 34.34, 'tube': 62.04, 'cone': 57.16, 'polycone': 116.12},
+    "sources_sha256": "76e9d0d63b2268d4487bf17bc51db7e11e496f00247adc8c5ffbb5284f2e4c3a",
+    "warp_inst_per_track": {'box': 18.61, 'trd': 34.34, 'tube': 62.04, 'cone': 57.16, 'polycone': 116.11},
     "profile": "profiles/query_fp32_passes_4M_counters.md",
 }
 KERNEL_SOURCES = ("solid_fp32.cuh", "query_fp32.cu", "gv_desc.h")

@@ -270,12 +270,14 @@ gv_status gv_debug_status(uint32_t* codes, int64_t* first_index, int32_t clear) 
   if (!codes || !first_index) return set_error(GV_ERR_INVALID_ARG, "gv_debug_status: NULL output");
 #ifdef GV_DEBUG
   cudaError_t e = cudaDeviceSynchronize();
-  unsigned long long w32[2] = {0ull, ~0ull}, w64[2] = {0ull, ~0ull};
+  unsigned long long w32[2] = {0ull, ~0ull}, w64[2] = {0ull, ~0ull}, ws[2] = {0ull, ~0ull};
   if (e == cudaSuccess) e = debug_read_query32(w32, clear != 0);
   if (e == cudaSuccess) e = debug_read_query64(w64, clear != 0);
+  if (e == cudaSuccess) e = debug_read_query_small(ws, clear != 0);
   if (e != cudaSuccess) return cuda_error(e, "gv_debug_status");
-  *codes = (uint32_t)(w32[0] | w64[0]);
-  const unsigned long long m = w32[1] < w64[1] ? w32[1] : w64[1];
+  *codes = (uint32_t)(w32[0] | w64[0] | ws[0]);
+  unsigned long long m = w32[1] < w64[1] ? w32[1] : w64[1];
+  if (ws[1] < m) m = ws[1];
   *first_index = m == ~0ull ? -1 : (int64_t)m;
   return GV_OK;
 #else

@@ -57,6 +57,7 @@ int sm_count();
 // The device-check words of the query passes' translation units (gv_debug.cuh).
 cudaError_t debug_read_query32(unsigned long long out[2], bool clear);
 cudaError_t debug_read_query64(unsigned long long out[2], bool clear);
+cudaError_t debug_read_query_small(unsigned long long out[2], bool clear);
 #endif
 
 // Launchers (async on `stream`); return cudaGetLastError() of the launch.
@@ -66,5 +67,8 @@ cudaError_t launch_query_fp64(const gv_solid* s, const QueryArgs& a, cudaStream_
 // (not the counter) and reports its number of blocks in *fused_blocks (0: the two-pass path).
 cudaError_t launch_query_fp32(const gv_solid* s, const QueryArgs& a, uint32_t* worklist,
                               unsigned long long* counter, cudaStream_t stream, int* fused_blocks = nullptr);
+// The one-launch pass when the basket qualifies (returns false and launches nothing otherwise).
+bool launch_query_small(const gv_solid* s, const QueryArgs& a, uint32_t* slots, cudaStream_t stream,
+                        int* fused_blocks);
 
 }  // namespace gv
